@@ -1,0 +1,117 @@
+"""Definition of the zero-temperature density matrix and its first-order response.
+
+Test infrastructure only (see the package docstring): nothing in the product path
+imports this module.
+
+All arithmetic is float64 NumPy/LAPACK.  The density matrix is the one the SP2
+chain converges to, written out from its definition:
+
+* Eq. DM-outer-product (section "The density matrix"):
+  D_ij = sum_k f_k c_i^(k) c_j^(k), with f_k = 1 for the n_occ lowest
+  eigenstates of the orthogonalised Hamiltonian and 0 for the others.
+* Eq. theta: D = theta(mu I - H), the step placed at the chemical potential mu
+  between the occupied and unoccupied eigenvalues.  mu is reported mid-gap; D
+  does not depend on where in the gap it sits.
+
+The response D1 = dD/dH [H1] and the adjoint dTr[D G]/dH are not given in the
+paper; they follow from first-order perturbation theory of a spectral projector:
+D1 = C (C^T H1 C  o  F) C^T with F_ij = (f_i - f_j)/(eps_i - eps_j) for
+f_i != f_j and 0 otherwise ("o" is the element-wise product).  This map is
+self-adjoint in the Frobenius inner product, so the adjoint of a symmetric weight
+G is the same formula applied to sym(G).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def eigensystem(H: np.ndarray):
+    """Ascending eigenvalues and orthonormal eigenvectors (columns) of symmetric H."""
+    H = np.asarray(H, dtype=np.float64)
+    lam, C = np.linalg.eigh(H)
+    return lam, C
+
+
+def occupations(n: int, n_occ: int) -> np.ndarray:
+    """f_k of Eq. DM-outer-product at zero temperature: 1 for the n_occ lowest states."""
+    if not 0 <= n_occ <= n:
+        raise ValueError("n_occ must lie in [0, n]")
+    f = np.zeros(n)
+    f[:n_occ] = 1.0
+    return f
+
+
+def density_from_eigensystem(C: np.ndarray, n_occ: int) -> np.ndarray:
+    """D_ij = sum_k f_k C_ik C_jk (Eq. DM-outer-product) for ascending columns C."""
+    c_occ = np.asarray(C, dtype=np.float64)[:, :n_occ]
+    return c_occ @ c_occ.T
+
+
+def density_matrix(H: np.ndarray, n_occ: int) -> np.ndarray:
+    """D = theta(mu I - H) (Eq. theta) by dense symmetric eigendecomposition."""
+    lam, C = eigensystem(H)
+    return density_from_eigensystem(C, n_occ)
+
+
+def density_rows(C: np.ndarray, n_occ: int, rows) -> np.ndarray:
+    """Selected rows of D from an eigensystem, one by one (for very large N)."""
+    c_occ = np.asarray(C, dtype=np.float64)[:, :n_occ]
+    rows = np.asarray(rows)
+    return c_occ[rows] @ c_occ.T
+
+
+def chemical_potential(lam: np.ndarray, n_occ: int) -> float:
+    """mu placed mid-gap between the highest occupied and lowest unoccupied eigenvalue."""
+    n = len(lam)
+    if n_occ == 0:
+        return -np.inf
+    if n_occ == n:
+        return np.inf
+    return 0.5 * (lam[n_occ - 1] + lam[n_occ])
+
+
+def homo_lumo_gap(lam: np.ndarray, n_occ: int) -> float:
+    if n_occ in (0, len(lam)):
+        return np.inf
+    return float(lam[n_occ] - lam[n_occ - 1])
+
+
+def band_energy(D: np.ndarray, H: np.ndarray) -> float:
+    """Tr[D H] in float64 for symmetric D and H (sum of element-wise products)."""
+    return float(np.sum(np.asarray(D, np.float64) * np.asarray(H, np.float64)))
+
+
+def response_weights(lam: np.ndarray, n_occ: int) -> np.ndarray:
+    """F_ij = (f_i - f_j)/(eps_i - eps_j) where f_i != f_j, else 0."""
+    n = len(lam)
+    f = occupations(n, n_occ)
+    df = f[:, None] - f[None, :]
+    de = lam[:, None] - lam[None, :]
+    cross = df != 0
+    if np.any(de[cross] == 0):
+        raise ValueError("no gap between occupied and unoccupied eigenvalues")
+    F = np.zeros((n, n))
+    F[cross] = df[cross] / de[cross]
+    return F
+
+
+def symmetrise(A: np.ndarray) -> np.ndarray:
+    A = np.asarray(A, dtype=np.float64)
+    return 0.5 * (A + A.T)
+
+
+def response(H: np.ndarray, H1: np.ndarray, n_occ: int) -> np.ndarray:
+    """First-order response D1 = dD/dH [H1] for a symmetric perturbation H1."""
+    lam, C = eigensystem(H)
+    return response_from_eigensystem(lam, C, H1, n_occ)
+
+
+def response_from_eigensystem(lam, C, H1, n_occ) -> np.ndarray:
+    F = response_weights(lam, n_occ)
+    h1 = C.T @ symmetrise(H1) @ C
+    return C @ (h1 * F) @ C.T
+
+
+def adjoint(H: np.ndarray, G: np.ndarray, n_occ: int) -> np.ndarray:
+    """Gradient of Tr[D(H) G] with respect to symmetric H (self-adjoint response)."""
+    return response(H, symmetrise(G), n_occ)

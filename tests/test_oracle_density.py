@@ -1,0 +1,157 @@
+"""Pins for oracle/density.py: closed forms, hand-derived fixtures and invariants.
+
+These tie the eigendecomposition definition of D = theta(mu I - H)
+(Eq. DM-outer-product, Eq. theta) and its perturbation-theory response to facts
+that do not come from the oracle itself.
+"""
+import numpy as np
+import pytest
+
+from oracle import density
+from paper_2107_02737_gb300 import inputs
+from tests._golden import load
+
+
+def test_golden_2x2():
+    g = load("density_2x2.txt")
+    H = g["H"].reshape(2, 2)
+    D = density.density_matrix(H, int(g["n_occ"]))
+    np.testing.assert_allclose(D, g["D"].reshape(2, 2), atol=1e-15)
+    lam, _ = density.eigensystem(H)
+    assert density.chemical_potential(lam, 1) == pytest.approx(g["mu"], abs=1e-15)
+    assert density.band_energy(D, H) == pytest.approx(g["band_energy"], abs=1e-14)
+
+
+def test_golden_3x3_rational_basis():
+    g = load("density_3x3.txt")
+    H = g["H9"].reshape(3, 3) / 9.0
+    lam, _ = density.eigensystem(H)
+    for k in (1, 2):
+        D = density.density_matrix(H, k)
+        np.testing.assert_allclose(D, g[f"D9_occ{k}"].reshape(3, 3) / 9.0, atol=1e-14)
+        assert density.chemical_potential(lam, k) == pytest.approx(g[f"mu_occ{k}"], abs=1e-14)
+        assert density.band_energy(D, H) == pytest.approx(g[f"band_energy_occ{k}"], abs=1e-14)
+
+
+def _closed_form_2x2(a, b, c):
+    # Lower eigenvector projector of [[a, b], [b, c]]: D = I/2 - (H - (a+c)/2 I)/(2r).
+    r = np.sqrt(((a - c) / 2) ** 2 + b * b)
+    H = np.array([[a, b], [b, c]])
+    return 0.5 * np.eye(2) - (H - 0.5 * (a + c) * np.eye(2)) / (2 * r)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_two_by_two_closed_form(seed):
+    a, b, c = np.random.default_rng(seed).normal(size=3)
+    H = np.array([[a, b], [b, c]])
+    np.testing.assert_allclose(density.density_matrix(H, 1), _closed_form_2x2(a, b, c), atol=1e-13)
+
+
+def test_two_by_two_response_is_derivative_of_closed_form():
+    a, b, c = 0.3, -0.7, 1.1
+    da, db, dc = 0.2, 0.5, -0.4
+    h = 1e-6
+    fd = (_closed_form_2x2(a + h * da, b + h * db, c + h * dc)
+          - _closed_form_2x2(a - h * da, b - h * db, c - h * dc)) / (2 * h)
+    H = np.array([[a, b], [b, c]])
+    H1 = np.array([[da, db], [db, dc]])
+    np.testing.assert_allclose(density.response(H, H1, 1), fd, atol=1e-8)
+
+
+def test_diagonal_hamiltonian():
+    rng = np.random.default_rng(3)
+    eps = rng.permutation(np.linspace(-2, 3, 9))
+    H = np.diag(eps)
+    n_occ = 4
+    D = density.density_matrix(H, n_occ)
+    expect = np.diag((eps <= np.sort(eps)[n_occ - 1]).astype(float))
+    np.testing.assert_allclose(D, expect, atol=1e-14)
+    assert density.band_energy(D, H) == pytest.approx(np.sort(eps)[:n_occ].sum(), abs=1e-13)
+
+
+def test_diagonal_response_closed_form():
+    rng = np.random.default_rng(4)
+    eps = np.array([-1.5, 0.7, -0.2, 2.0, 0.1, -0.9])
+    H = np.diag(eps)
+    H1 = inputs.symmetric_gaussian(6, rng)
+    n_occ = 3
+    f = (eps <= np.sort(eps)[n_occ - 1]).astype(float)
+    expect = np.zeros((6, 6))
+    for i in range(6):
+        for j in range(6):
+            if f[i] != f[j]:
+                expect[i, j] = H1[i, j] * (f[i] - f[j]) / (eps[i] - eps[j])
+    np.testing.assert_allclose(density.response(H, H1, n_occ), expect, atol=1e-14)
+
+
+@pytest.fixture(scope="module")
+def gapped():
+    return inputs.gapped_random(48, 20, np.random.default_rng(11))
+
+
+def test_invariants(gapped):
+    H, n_occ = gapped.H, gapped.n_occ
+    D = density.density_matrix(H, n_occ)
+    np.testing.assert_allclose(D @ D, D, atol=1e-13)
+    assert np.trace(D) == pytest.approx(n_occ, abs=1e-12)
+    np.testing.assert_allclose(H @ D - D @ H, 0, atol=1e-13)
+    np.testing.assert_allclose(D, D.T, atol=1e-15)
+
+
+def test_agrees_with_generator_eigensystem(gapped):
+    # The generator builds H from a known spectrum; D and Tr[DH] follow from it directly.
+    D = density.density_matrix(gapped.H, gapped.n_occ)
+    np.testing.assert_allclose(D, density.density_from_eigensystem(gapped.eigvecs, gapped.n_occ), atol=1e-12)
+    assert density.band_energy(D, gapped.H) == pytest.approx(gapped.eigvals[:gapped.n_occ].sum(), abs=1e-11)
+
+
+def test_scale_and_shift_invariance(gapped):
+    D = density.density_matrix(gapped.H, gapped.n_occ)
+    D2 = density.density_matrix(2.5 * gapped.H - 0.7 * np.eye(gapped.n), gapped.n_occ)
+    np.testing.assert_allclose(D2, D, atol=1e-12)
+
+
+def test_particle_hole(gapped):
+    n = gapped.n
+    D = density.density_matrix(gapped.H, gapped.n_occ)
+    Dm = density.density_matrix(-gapped.H, n - gapped.n_occ)
+    np.testing.assert_allclose(Dm, np.eye(n) - D, atol=1e-12)
+
+
+def test_permutation_covariance(gapped):
+    perm = np.random.default_rng(5).permutation(gapped.n)
+    P = np.eye(gapped.n)[perm]
+    D = density.density_matrix(gapped.H, gapped.n_occ)
+    np.testing.assert_allclose(density.density_matrix(P @ gapped.H @ P.T, gapped.n_occ), P @ D @ P.T, atol=1e-12)
+
+
+def test_response_matches_central_differences(gapped):
+    rng = np.random.default_rng(6)
+    H1 = inputs.symmetric_gaussian(gapped.n, rng) * 0.1
+    h = 1e-5
+    fd = (density.density_matrix(gapped.H + h * H1, gapped.n_occ)
+          - density.density_matrix(gapped.H - h * H1, gapped.n_occ)) / (2 * h)
+    D1 = density.response(gapped.H, H1, gapped.n_occ)
+    np.testing.assert_allclose(D1, fd, atol=1e-8)
+    # D1 is symmetric and keeps the trace (the occupation is fixed).
+    np.testing.assert_allclose(D1, D1.T, atol=1e-14)
+    assert abs(np.trace(D1)) < 1e-12
+
+
+def test_adjoint_duality_and_differences(gapped):
+    rng = np.random.default_rng(7)
+    G = rng.standard_normal((gapped.n, gapped.n))  # not symmetric on purpose
+    E = inputs.symmetric_gaussian(gapped.n, rng)
+    grad = density.adjoint(gapped.H, G, gapped.n_occ)
+    lhs = np.sum(E * grad)
+    rhs = np.sum(G * density.response(gapped.H, E, gapped.n_occ))
+    assert lhs == pytest.approx(rhs, rel=1e-11)
+    h = 1e-5
+    f = lambda s: np.sum(density.density_matrix(gapped.H + s * E, gapped.n_occ) * G)
+    assert lhs == pytest.approx((f(h) - f(-h)) / (2 * h), rel=1e-6)
+
+
+def test_no_gap_is_rejected():
+    H = np.diag([0.0, 1.0, 1.0, 2.0])
+    with pytest.raises(ValueError):
+        density.response(H, np.eye(4), 2)
