@@ -1,0 +1,221 @@
+/*
+ * sp2.h -- C ABI of libsp2, the GB300 (sm_103a) DNN-SP2 density-matrix library.
+ *
+ * The library maps an orthogonalised, symmetric N x N Hamiltonian H to the
+ * zero-temperature density matrix D = theta(mu I - H) (section "The density
+ * matrix", Eq. theta) by the deep-network form of the second-order spectral
+ * projection chain (section "Deep-neural network electronic structure solver",
+ * Eq. Deep_NN): X_0 = (eps_max I - H)/(eps_max - eps_min), then per layer
+ * X_{n+1} = X_n^2 or 2 X_n - X_n^2, the sign chosen from traces so that Tr X
+ * moves toward the occupation, until X is idempotent.  The matrix square is the
+ * activation f(X) = X^2; in the split precisions it is evaluated from a
+ * two-term 16-bit representation X = X^(0) + X^(1) with FP32 accumulation
+ * (Eq. activ).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are dense, row-major, N x N, with leading dimension N.
+ *  - Matrix pointers may be device pointers or host pointers (pageable or
+ *    pinned); the library detects which and stages host data through device
+ *    memory.  The caller owns every buffer it passes; the library frees none.
+ *  - H must be symmetric (bit-exactly, as produced by (A + A^T)/2); the result
+ *    for an asymmetric H is unspecified but finite.
+ *  - `n_occ` must be an integer value in [0, N].  n_occ = 0 gives D = 0 and
+ *    n_occ = N gives D = I without layers.
+ *  - `workspace` may be NULL, in which case the call allocates device memory
+ *    and frees it before returning; otherwise it must be a device pointer of
+ *    at least the size the matching *_workspace_bytes function returns,
+ *    256-byte aligned.  Host-resident matrices are staged in the workspace
+ *    beyond that size when it is large enough (8 bytes per FP64 and 4 per FP32
+ *    element, each piece rounded up to 256 bytes), else in memory the call
+ *    allocates and frees.
+ *  - Calls are stream-ordered on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) and synchronise that stream before returning, because
+ *    the status and the statistics are read back to the host.
+ *  - A wait inside a kernel (the grid barrier between layers, a pipeline
+ *    barrier) that exceeds `timeout_ms` makes the kernel stop and the call
+ *    return SP2_ERR_TIMEOUT; no call leaves a kernel spinning.
+ *  - Errors never leave partially written output undefined in size: on any
+ *    status other than SP2_OK / SP2_ERR_NOT_CONVERGED the contents of the
+ *    output matrices are unspecified.
+ */
+#ifndef SP2_H
+#define SP2_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SP2_OK = 0,
+    SP2_ERR_ARG = 1,            /* invalid argument (size, n_occ, pointer, option) */
+    SP2_ERR_NONFINITE = 2,      /* H (or H1 / G) contains NaN or Inf */
+    SP2_ERR_NOT_CONVERGED = 3,  /* max_layers reached before the stop rule fired; output holds the last layer */
+    SP2_ERR_TIMEOUT = 4,        /* a device-side wait gave up after timeout_ms */
+    SP2_ERR_CUDA = 5,           /* a CUDA runtime or driver call failed */
+    SP2_ERR_NOMEM = 6,          /* device or host allocation failed */
+    SP2_ERR_UNSUPPORTED = 7     /* the device is not sm_103 or lacks a needed feature */
+} sp2_status;
+
+typedef enum {
+    SP2_FP32_SIMT = 0,   /* X^2 with FP32 CUDA-core FMAs, FP32 storage */
+    SP2_FP16_SPLIT = 1,  /* X = hi + lo in FP16 (lo kept scaled by 2^11), tensor cores, FP32 accumulation */
+    SP2_BF16_SPLIT = 2   /* X = hi + lo in BF16, tensor cores, FP32 accumulation */
+} sp2_precision;
+
+/* Stop reasons (sp2_stats.stop_reason). */
+#define SP2_STOP_NONE 0     /* the chain did not end by its own rule (forced sequence ran out) */
+#define SP2_STOP_TOL 1      /* |Tr X - ||X||_F^2| <= tol */
+#define SP2_STOP_STALL 2    /* |Tr X - ||X||_F^2| <= 1e-2 and no smaller than two layers earlier */
+#define SP2_STOP_MAX 3      /* max_layers reached (status SP2_ERR_NOT_CONVERGED) */
+#define SP2_STOP_TRIVIAL 4  /* n_occ = 0 or n_occ = N */
+
+/* Layer choices (sp2_layer_stat.choice). */
+#define SP2_CHOICE_INPUT (-1)  /* X_0 */
+#define SP2_CHOICE_SQUARE 0    /* X_{n+1} = X_n^2 */
+#define SP2_CHOICE_FLIP 1      /* X_{n+1} = 2 X_n - X_n^2 */
+
+#define SP2_MAX_LAYERS_LIMIT 200
+
+/* Statistics of one layer X_n, reduced in FP64 from the stored FP32 X_n. */
+typedef struct {
+    double trace;     /* Tr X_n */
+    double trace_sq;  /* ||X_n||_F^2 = Tr X_n^2 for symmetric X_n */
+    double idem;      /* Tr X_n - ||X_n||_F^2 = sum_i lambda_i (1 - lambda_i) */
+    int choice;       /* SP2_CHOICE_* that produced X_n */
+    int reserved;
+} sp2_layer_stat;
+
+/* Result record, caller-owned host memory.  `layer` may be NULL; otherwise it
+ * points to `layer_cap` entries and receives min(layers + 1, layer_cap) of them
+ * (entry 0 is the input layer). */
+typedef struct {
+    int layers;            /* number of square layers applied */
+    int stop_reason;       /* SP2_STOP_* */
+    double eps_min;        /* spectral bounds used for X_0 */
+    double eps_max;
+    double band_energy;    /* Tr[D H] in FP64 from the FP32 D */
+    double trace_D;        /* Tr D in FP64 from the FP32 D */
+    sp2_layer_stat *layer;
+    int layer_cap;
+    int reserved;
+    float phase_ms[4];     /* with sp2_opts.profile: device time of [0] bounds + input layer
+                              (+ response / adjoint stream start), [1] the persistent layer
+                              kernel, [2] output copy and FP64 reductions, [3] all three;
+                              CUDA events on the call's stream */
+} sp2_stats;
+
+/* Options; pass NULL for the defaults listed. */
+typedef struct {
+    int precision;        /* sp2_precision, default SP2_FP16_SPLIT */
+    int max_layers;       /* default 100, at most SP2_MAX_LAYERS_LIMIT */
+    double timeout_ms;    /* device wait limit, default 2000 */
+    int user_bounds;      /* 0 = Gershgorin bounds (default), 1 = use eps_min / eps_max below */
+    int test_hook;        /* 0 in normal use; 1 = CTA 0 withholds its first grid-barrier arrival, so
+                             the barrier wait must run out (tests the timeout path) */
+    double eps_min;
+    double eps_max;
+    int profile;          /* 1 = record per-phase device times into sp2_stats.phase_ms */
+    int reserved2;
+} sp2_opts;
+
+/* Fill `o` with the defaults. */
+void sp2_default_opts(sp2_opts *o);
+
+/* Human-readable name of a status code (static storage). */
+const char *sp2_status_string(sp2_status s);
+
+/* Device bytes sp2_density needs as workspace for size N (device-resident H and D). */
+size_t sp2_density_workspace_bytes(int N, const sp2_opts *o);
+
+/*
+ * sp2_density -- D = theta(mu I - H) by the DNN-SP2 chain.
+ *   H      [in]  N x N symmetric, FP64.
+ *   N      [in]  matrix size, 1 <= N <= 65536.
+ *   n_occ  [in]  number of occupied states (integer value).
+ *   tol    [in]  stop when |Tr X_n - ||X_n||_F^2| <= tol (the paper's trace-based
+ *                idempotency estimate, section "GPU and tensor core performance").
+ *   D      [out] N x N FP32, the last layer X_L.
+ *   st     [out] statistics (may be NULL).
+ * Returns SP2_OK when the stop rule fired, SP2_ERR_NOT_CONVERGED when max_layers
+ * was reached (D holds X_max), or an error.
+ */
+sp2_status sp2_density(const double *H, int N, double n_occ, double tol, float *D,
+                       sp2_stats *st, const sp2_opts *o, void *workspace, size_t ws_bytes,
+                       void *stream);
+
+/* Device bytes sp2_response needs as workspace. */
+size_t sp2_response_workspace_bytes(int N, const sp2_opts *o);
+
+/*
+ * sp2_response -- first-order response D1 = dD/dH [H1] of the chain.
+ * The chain is differentiated layer by layer with the layer signs held fixed:
+ * X1_0 = -H1/(eps_max - eps_min), and per layer with C = X_n X1_n,
+ * X1_{n+1} = C + C^T (X^2 layers) or 2 X1_n - (C + C^T) (2X - X^2 layers).
+ * The forward chain runs alongside and takes its own decisions exactly as
+ * sp2_density does, unless `fwd` (statistics of an earlier sp2_density call on
+ * the same H, with its `layer` array filled) is given: then the forward replays
+ * fwd's layer sequence and bounds.  The paper gives no response; this is the
+ * derivative of its chain.
+ *   H1  [in]  N x N symmetric FP64 perturbation.
+ *   D   [out] N x N FP32 density matrix (may be NULL).
+ *   D1  [out] N x N FP32 response.
+ */
+sp2_status sp2_response(const double *H, const double *H1, int N, double n_occ, double tol,
+                        const sp2_stats *fwd, float *D, float *D1, sp2_stats *st,
+                        const sp2_opts *o, void *workspace, size_t ws_bytes, void *stream);
+
+/* Device bytes sp2_adjoint needs for a chain of `layers` layers. */
+size_t sp2_adjoint_workspace_bytes(int N, int layers, const sp2_opts *o);
+
+/*
+ * sp2_adjoint -- gradient dTr[D G]/dH of the chain, by reverse accumulation.
+ * Runs the forward chain storing every layer's split operands (replaying `fwd`
+ * when given, else deciding as sp2_density), then G_L = (G + G^T)/2 and, for
+ * the layer that made X_{n+1} from X_n, G_n = G_{n+1} X_n + X_n G_{n+1} (X^2)
+ * or 2 G_{n+1} - (G_{n+1} X_n + X_n G_{n+1}) (2X - X^2), and returns
+ * dH = -G_0/(eps_max - eps_min).  Layer signs and bounds are held constant.
+ *   G   [in]  N x N FP64 weight (need not be symmetric).
+ *   dH  [out] N x N FP32 gradient (symmetric).
+ */
+sp2_status sp2_adjoint(const double *H, const double *G, int N, double n_occ, double tol,
+                       const sp2_stats *fwd, float *D, float *dH, sp2_stats *st,
+                       const sp2_opts *o, void *workspace, size_t ws_bytes, void *stream);
+
+/* Device bytes sp2_density_batched needs. */
+size_t sp2_density_batched_workspace_bytes(int B, const int *N, const sp2_opts *o);
+
+/*
+ * sp2_density_batched -- B independent chains in one persistent grouped launch.
+ * H[b], D[b] are per-instance pointers (host arrays of B pointers, each matrix
+ * device- or host-resident as above), N[b] and n_occ[b] per instance, st[b]
+ * per-instance statistics (st may be NULL).  Every instance takes its own layer
+ * sequence; an instance that has stopped drops out of the schedule.  Returns
+ * the worst status over the instances (errors before NOT_CONVERGED).
+ */
+sp2_status sp2_density_batched(int B, const double *const *H, const int *N, const double *n_occ,
+                               double tol, float *const *D, sp2_stats *st, const sp2_opts *o,
+                               void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * sp2_apply_layers -- apply a given layer sequence to a given X_0 (test and
+ * tooling entry point: the matrix-square kernel without the input layer).
+ *   X0       [in]  N x N FP32 symmetric start matrix.
+ *   choices  [in]  host array of n_layers SP2_CHOICE_SQUARE / SP2_CHOICE_FLIP.
+ *   X        [out] N x N FP32 result X_{n_layers}.
+ *   st       [out] per-layer traces (stop fields unused).
+ */
+sp2_status sp2_apply_layers(const float *X0, int N, const int *choices, int n_layers, float *X,
+                            sp2_stats *st, const sp2_opts *o, void *stream);
+
+/* Number of streaming multiprocessors and whether the current device runs this
+ * library's kernels (compute capability 10.3). */
+sp2_status sp2_device_info(int *sm_count, int *cc_major, int *cc_minor);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP2_H */

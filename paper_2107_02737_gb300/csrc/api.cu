@@ -1,0 +1,763 @@
+// api.cu -- the C ABI declared in include/sp2.h.
+//
+// Every entry point goes through one runner: validate, lay out the workspace,
+// stage host matrices, encode the TMA tensor maps, launch
+//   Gershgorin bounds -> input layer -> [response / adjoint stream start]
+//   -> one cooperative persistent kernel for all layers -> output copy + FP64
+//   Tr[DH], Tr D
+// on the caller's stream, then read the per-instance control blocks back.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "device_common.cuh"
+
+using namespace sp2i;
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// 2-D map over an np x np 16-bit matrix, box 64 (K, inner) x 128 rows, 128B swizzle.
+bool encode_op_map(CUtensorMap *m, const void *base, int np, int precision) {
+    EncodeTiledFn fn = get_encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)np};
+    cuuint64_t strides[1] = {(cuuint64_t)np * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)(TC_BN / 2)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, precision == SP2_BF16_SPLIT ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct DeviceInfo {
+    int sm = 0, major = 0, minor = 0;
+    cudaError_t err = cudaSuccess;
+};
+
+DeviceInfo query_device() {
+    DeviceInfo di;
+    int dev = 0;
+    di.err = cudaGetDevice(&dev);
+    if (di.err != cudaSuccess) return di;
+    di.err = cudaDeviceGetAttribute(&di.sm, cudaDevAttrMultiProcessorCount, dev);
+    if (di.err != cudaSuccess) return di;
+    di.err = cudaDeviceGetAttribute(&di.major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (di.err != cudaSuccess) return di;
+    di.err = cudaDeviceGetAttribute(&di.minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return di;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+sp2_opts resolve_opts(const sp2_opts *o) {
+    sp2_opts r;
+    sp2_default_opts(&r);
+    if (o) r = *o;
+    return r;
+}
+
+struct InstSpec {
+    int n = 0;
+    double n_occ = 0;
+    const double *H = nullptr;
+    const double *H1 = nullptr;    // response H1 / adjoint G
+    const float *X0 = nullptr;     // apply mode
+    float *D = nullptr;
+    float *D1 = nullptr;
+    sp2_stats *st = nullptr;
+    const sp2_stats *fwd = nullptr;
+    const int *choices = nullptr;  // apply mode (host)
+    int nchoices = -1;
+};
+
+// Device allocation owned by one call; freed on every exit path.
+struct Arena {
+    std::vector<void *> ptrs;
+    cudaStream_t s;
+    explicit Arena(cudaStream_t st) : s(st) {}
+    void *get(size_t bytes) {
+        void *p = nullptr;
+        if (bytes == 0) bytes = 256;
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return p;
+    }
+    ~Arena() {
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+        cudaStreamSynchronize(s);
+    }
+};
+
+struct Carver {
+    uint8_t *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((uint8_t *)b) {}
+    void *take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+// Tile tables: SIMT uses square 128-tiles with bi <= bj; the tensor-core path
+// uses 128 x 256 tiles containing at least one element with row <= column.
+void build_tiles(int path, int np, std::vector<int2> &t) {
+    if (path == PATH_SIMT) {
+        const int nb = np / SIMT_T;
+        for (int bj = 0; bj < nb; ++bj)
+            for (int bi = 0; bi <= bj; ++bi) t.push_back(make_int2(bi, bj));
+    } else {
+        const int nbi = np / TC_BM, nbj = (np + TC_BN - 1) / TC_BN;
+        for (int bj = 0; bj < nbj; ++bj)
+            for (int bi = 0; bi < nbi && bi * TC_BM < (bj + 1) * TC_BN; ++bi) t.push_back(make_int2(bi, bj));
+    }
+}
+
+int ntiles_for(int path, int np) {
+    std::vector<int2> t;
+    build_tiles(path, np, t);
+    return (int)t.size();
+}
+
+int init_blocks_host(int np) {
+    size_t work = (size_t)np * np / 4, per = 256 * 8;
+    size_t g = (work + per - 1) / per;
+    if (g < 1) g = 1;
+    if (g > (size_t)INIT_BLOCKS_MAX) g = INIT_BLOCKS_MAX;
+    return (int)g;
+}
+
+struct Plan {
+    int mode, path, precision;
+    std::vector<InstSpec> inst;       // non-trivial instances, in launch order
+    std::vector<int> slots;           // nslots_x per instance
+    int max_np = 0, max_n = 0;
+};
+
+size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr) {
+    (void)offsets_unused;
+    Carver c(nullptr);
+    const int B = (int)pl.inst.size();
+    c.take(sizeof(InstDesc) * B);
+    int tiles = 0;
+    for (auto &s : pl.inst) tiles += ntiles_for(pl.path, round_up(s.n, PAD));
+    c.take(sizeof(int2) * tiles);
+    c.take(64);                           // barrier + err
+    c.take(sizeof(int) * (MAX_L + 1));    // forced choices
+    const int initb = init_blocks_host(pl.max_np);
+    for (int i = 0; i < B; ++i) {
+        const int np = round_up(pl.inst[i].n, PAD);
+        const size_t mat = (size_t)np * np;
+        const int nt = ntiles_for(pl.path, np);
+        const int cap = std::max(nt, initb);
+        c.take(sizeof(InstCtl));
+        c.take(sizeof(Part) * cap);
+        c.take(sizeof(Part) * cap);
+        c.take(sizeof(double2) * FIN_BLOCKS_MAX);
+        c.take(mat * 4);
+        c.take(mat * 4);
+        if (pl.path == PATH_TC) {
+            c.take((size_t)pl.slots[i] * 3 * mat * 2);
+            c.take((size_t)pl.slots[i] * 3 * sizeof(CUtensorMap));
+            if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
+                c.take(mat * 4);
+                c.take(mat * 4);
+                c.take(2 * 3 * mat * 2);
+                c.take(6 * sizeof(CUtensorMap));
+            }
+        }
+    }
+    return c.off + 256;
+}
+
+void fill_stats(sp2_stats *st, const InstCtl &ctl) {
+    if (!st) return;
+    st->layers = ctl.layers;
+    st->stop_reason = ctl.stop_reason;
+    st->eps_min = ctl.eps_min;
+    st->eps_max = ctl.eps_max;
+    st->band_energy = ctl.band_energy;
+    st->trace_D = ctl.trace_D;
+    if (st->layer && st->layer_cap > 0) {
+        const int cnt = std::min(ctl.layers + 1, st->layer_cap);
+        for (int k = 0; k < cnt; ++k) {
+            st->layer[k].trace = ctl.stat[k].trace;
+            st->layer[k].trace_sq = ctl.stat[k].trace_sq;
+            st->layer[k].idem = ctl.stat[k].idem;
+            st->layer[k].choice = ctl.stat[k].choice;
+            st->layer[k].reserved = 0;
+        }
+    }
+}
+
+void fill_trivial_stats(sp2_stats *st, int n, double n_occ) {
+    if (!st) return;
+    st->layers = 0;
+    st->stop_reason = SP2_STOP_TRIVIAL;
+    st->eps_min = st->eps_max = 0.0;
+    st->band_energy = 0.0;  // filled by the caller when H is at hand
+    st->trace_D = n_occ;
+    (void)n;
+    if (st->layer && st->layer_cap > 0) {
+        st->layer[0].trace = n_occ;
+        st->layer[0].trace_sq = n_occ;
+        st->layer[0].idem = 0.0;
+        st->layer[0].choice = SP2_CHOICE_INPUT;
+        st->layer[0].reserved = 0;
+    }
+}
+
+int status_rank(int s) {
+    // errors first, then NOT_CONVERGED, then OK
+    if (s == SP2_OK) return 0;
+    if (s == SP2_ERR_NOT_CONVERGED) return 1;
+    return 2;
+}
+
+#define CK(x)                                  \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) {               \
+            cudaGetLastError();                \
+            return SP2_ERR_CUDA;               \
+        }                                      \
+    } while (0)
+
+sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws_bytes, cudaStream_t s) {
+    const int B = (int)pl.inst.size();
+    if (B == 0) return SP2_OK;
+    DeviceInfo di = query_device();
+    if (di.err != cudaSuccess) return SP2_ERR_CUDA;
+    if (di.major != 10 || di.minor != 3) return SP2_ERR_UNSUPPORTED;
+    if (pl.path == PATH_TC && !get_encode_fn()) return SP2_ERR_UNSUPPORTED;
+
+    Arena arena(s);
+    const size_t need = plan_bytes(pl);
+    if (ws && ws_bytes < need) return SP2_ERR_ARG;
+    if (ws && ((uintptr_t)ws & 255)) return SP2_ERR_ARG;
+    if (!ws) {
+        ws = arena.get(need);
+        if (!ws) return SP2_ERR_NOMEM;
+    }
+    Carver c(ws);
+    InstDesc *d_inst = (InstDesc *)c.take(sizeof(InstDesc) * B);
+    std::vector<std::vector<int2>> tiles(B);
+    int total_tiles = 0;
+    for (int i = 0; i < B; ++i) {
+        build_tiles(pl.path, round_up(pl.inst[i].n, PAD), tiles[i]);
+        total_tiles += (int)tiles[i].size();
+    }
+    int2 *d_tiles = (int2 *)c.take(sizeof(int2) * total_tiles);
+    uint8_t *d_sync = (uint8_t *)c.take(64);
+    int *d_forced = (int *)c.take(sizeof(int) * (MAX_L + 1));
+
+    std::vector<InstDesc> h_inst(B);
+    std::vector<InstCtl> h_ctl(B);
+    std::vector<int2> h_tiles;
+    std::vector<std::vector<CUtensorMap>> h_xmaps(B), h_ymaps(B);
+    std::vector<CUtensorMap *> d_xmaps(B, nullptr), d_ymaps(B, nullptr);
+    std::vector<InstCtl *> d_ctl(B);
+    std::vector<int> forced;
+    const int initb = init_blocks_host(pl.max_np);
+    bool user_bounds = o.user_bounds != 0;
+
+    for (int i = 0; i < B; ++i) {
+        InstSpec &sp = pl.inst[i];
+        InstDesc &d = h_inst[i];
+        memset(&d, 0, sizeof(d));
+        const int n = sp.n, np = round_up(n, PAD);
+        const size_t mat = (size_t)np * np;
+        d.n = n;
+        d.np = np;
+        d.ntiles = (int)tiles[i].size();
+        d.tile_off = (int)h_tiles.size();
+        h_tiles.insert(h_tiles.end(), tiles[i].begin(), tiles[i].end());
+        d.n_occ = sp.n_occ;
+        d.nforced = -1;
+        d.nslots_x = pl.slots[i];
+        d.part_cap = std::max(d.ntiles, initb);
+        d.fin_blocks = FIN_BLOCKS_MAX;
+        d_ctl[i] = (InstCtl *)c.take(sizeof(InstCtl));
+        d.ctl = d_ctl[i];
+        d.part[0] = (Part *)c.take(sizeof(Part) * d.part_cap);
+        d.part[1] = (Part *)c.take(sizeof(Part) * d.part_cap);
+        d.fin_part = (double2 *)c.take(sizeof(double2) * FIN_BLOCKS_MAX);
+        d.xf[0] = (float *)c.take(mat * 4);
+        d.xf[1] = (float *)c.take(mat * 4);
+        if (pl.path == PATH_TC) {
+            d.xop = (uint16_t *)c.take((size_t)d.nslots_x * 3 * mat * 2);
+            d_xmaps[i] = (CUtensorMap *)c.take((size_t)d.nslots_x * 3 * sizeof(CUtensorMap));
+            d.xmap = d_xmaps[i];
+            h_xmaps[i].resize((size_t)d.nslots_x * 3);
+            for (int sl = 0; sl < d.nslots_x; ++sl)
+                for (int k = 0; k < 3; ++k) {
+                    // BF16 keeps op0 == op1: the map of op0 points at op1's matrix.
+                    const int src = (pl.precision == SP2_BF16_SPLIT && k == 0) ? 1 : k;
+                    if (!encode_op_map(&h_xmaps[i][sl * 3 + k], d.xop + ((size_t)sl * 3 + src) * mat, np,
+                                       pl.precision))
+                        return SP2_ERR_UNSUPPORTED;
+                }
+            if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
+                d.yf[0] = (float *)c.take(mat * 4);
+                d.yf[1] = (float *)c.take(mat * 4);
+                d.yop = (uint16_t *)c.take(2 * 3 * mat * 2);
+                d_ymaps[i] = (CUtensorMap *)c.take(6 * sizeof(CUtensorMap));
+                d.ymap = d_ymaps[i];
+                h_ymaps[i].resize(6);
+                for (int sl = 0; sl < 2; ++sl)
+                    for (int k = 0; k < 3; ++k)
+                        if (!encode_op_map(&h_ymaps[i][sl * 3 + k], d.yop + ((size_t)sl * 3 + k) * mat, np,
+                                           pl.precision))
+                            return SP2_ERR_UNSUPPORTED;
+            }
+        }
+        InstCtl &ctl = h_ctl[i];
+        memset(&ctl, 0, sizeof(ctl));
+        ctl.emin_key = dkey(INFINITY);
+        ctl.emax_key = dkey(-INFINITY);
+        ctl.ymax_key = dkey(0.0);
+        ctl.y_scale = 1.0;
+        ctl.layers = 0;
+        // Replayed layer sequence and bounds (response / adjoint following an
+        // earlier forward run, or the layer-application entry point).
+        if (sp.fwd) {
+            user_bounds = true;
+            ctl.eps_min = sp.fwd->eps_min;
+            ctl.eps_max = sp.fwd->eps_max;
+            forced.assign(sp.fwd->layers, 0);
+            for (int k = 0; k < sp.fwd->layers; ++k) forced[k] = sp.fwd->layer[k + 1].choice;
+            d.nforced = sp.fwd->layers;
+            d.forced = d_forced;
+        } else if (sp.choices) {
+            forced.assign(sp.choices, sp.choices + sp.nchoices);
+            d.nforced = sp.nchoices;
+            d.forced = d_forced;
+        } else if (user_bounds) {
+            ctl.eps_min = o.eps_min;
+            ctl.eps_max = o.eps_max;
+        }
+        d.H = sp.H;
+        d.H1 = sp.H1;
+        d.out = sp.D;
+        d.out1 = sp.D1;
+    }
+
+    // Stage host-resident inputs and outputs through device memory: from the
+    // tail of the caller's workspace when it has room, else a stream-ordered
+    // allocation freed before the call returns.
+    const size_t ws_end = ws_bytes;
+    auto staging = [&](size_t bytes) -> void * {
+        const size_t start = (c.off + 255) & ~(size_t)255;
+        if (ws_end && start + bytes <= ws_end) return c.take(bytes);
+        return arena.get(bytes);
+    };
+    std::vector<std::pair<float *, float *>> copy_back;  // (host, device staging)
+    std::vector<size_t> copy_back_n;
+    for (int i = 0; i < B; ++i) {
+        InstSpec &sp = pl.inst[i];
+        InstDesc &d = h_inst[i];
+        const size_t nn = (size_t)sp.n * sp.n;
+        if (sp.H && !is_device_ptr(sp.H)) {
+            double *t = (double *)staging(nn * 8);
+            if (!t) return SP2_ERR_NOMEM;
+            CK(cudaMemcpyAsync(t, sp.H, nn * 8, cudaMemcpyHostToDevice, s));
+            d.H = t;
+        }
+        if (sp.H1 && !is_device_ptr(sp.H1)) {
+            double *t = (double *)staging(nn * 8);
+            if (!t) return SP2_ERR_NOMEM;
+            CK(cudaMemcpyAsync(t, sp.H1, nn * 8, cudaMemcpyHostToDevice, s));
+            d.H1 = t;
+        }
+        if (sp.X0 && !is_device_ptr(sp.X0)) {
+            float *t = (float *)staging(nn * 4);
+            if (!t) return SP2_ERR_NOMEM;
+            CK(cudaMemcpyAsync(t, sp.X0, nn * 4, cudaMemcpyHostToDevice, s));
+            sp.X0 = t;
+        }
+        if (sp.D && !is_device_ptr(sp.D)) {
+            float *t = (float *)staging(nn * 4);
+            if (!t) return SP2_ERR_NOMEM;
+            copy_back.push_back({sp.D, t});
+            copy_back_n.push_back(nn);
+            d.out = t;
+        }
+        if (sp.D1 && !is_device_ptr(sp.D1)) {
+            float *t = (float *)staging(nn * 4);
+            if (!t) return SP2_ERR_NOMEM;
+            copy_back.push_back({sp.D1, t});
+            copy_back_n.push_back(nn);
+            d.out1 = t;
+        }
+    }
+
+    // Upload descriptors, tables and control blocks.
+    CK(cudaMemcpyAsync(d_inst, h_inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_tiles, h_tiles.data(), sizeof(int2) * h_tiles.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d_sync, 0, 64, s));
+    if (!forced.empty())
+        CK(cudaMemcpyAsync(d_forced, forced.data(), sizeof(int) * forced.size(), cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < B; ++i) {
+        CK(cudaMemcpyAsync(d_ctl[i], &h_ctl[i], sizeof(InstCtl), cudaMemcpyHostToDevice, s));
+        if (d_xmaps[i])
+            CK(cudaMemcpyAsync(d_xmaps[i], h_xmaps[i].data(), h_xmaps[i].size() * sizeof(CUtensorMap),
+                               cudaMemcpyHostToDevice, s));
+        if (d_ymaps[i])
+            CK(cudaMemcpyAsync(d_ymaps[i], h_ymaps[i].data(), h_ymaps[i].size() * sizeof(CUtensorMap),
+                               cudaMemcpyHostToDevice, s));
+    }
+
+    // Optional per-phase device timing on the call's stream.
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int k = 0; k < 4; ++k)
+                if (e[k]) cudaEventDestroy(e[k]);
+        }
+    } ev_guard{ev};
+    if (o.profile)
+        for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ev[k]));
+    if (o.profile) CK(cudaEventRecord(ev[0], s));
+
+    // Input layer.
+    if (pl.mode == MODE_APPLY) {
+        CK(launch_init_x_from(d_inst, pl.inst[0].X0, pl.max_np, pl.path, pl.precision, s));
+    } else {
+        CK(launch_gershgorin(d_inst, B, pl.max_n, user_bounds, s));
+        CK(launch_init_x(d_inst, B, pl.max_np, pl.path, pl.precision, user_bounds, s));
+    }
+    if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
+        CK(launch_maxabs(d_inst, B, pl.max_n, s));
+        CK(launch_init_y(d_inst, pl.mode, pl.precision, s));
+    }
+
+    // The layer loop.
+    RunParams rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.inst = d_inst;
+    rp.tiles = d_tiles;
+    rp.barrier = (unsigned int *)d_sync;
+    rp.err = (int *)(d_sync + 4);
+    rp.tol = tol;
+    rp.timeout_ns = (unsigned long long)(o.timeout_ms * 1e6);
+    rp.B = B;
+    rp.mode = pl.mode;
+    rp.precision = pl.precision;
+    rp.max_layers = o.max_layers;
+    rp.test_hook = o.test_hook;
+    int per_sm = (pl.path == PATH_TC) ? tc_blocks_per_sm() : simt_blocks_per_sm();
+    if (per_sm <= 0) return SP2_ERR_UNSUPPORTED;
+    if (pl.path == PATH_TC) per_sm = 1;
+    const int grid = per_sm * di.sm;
+    if (o.profile) CK(cudaEventRecord(ev[1], s));
+    CK(pl.path == PATH_TC ? launch_tc_persistent(rp, grid, s) : launch_simt_persistent(rp, grid, s));
+    if (o.profile) CK(cudaEventRecord(ev[2], s));
+
+    CK(launch_finalize(d_inst, B, pl.max_n, pl.mode == MODE_APPLY ? MODE_DENSITY : pl.mode, s));
+    if (o.profile) CK(cudaEventRecord(ev[3], s));
+    for (size_t k = 0; k < copy_back.size(); ++k)
+        CK(cudaMemcpyAsync(copy_back[k].first, copy_back[k].second, copy_back_n[k] * 4, cudaMemcpyDeviceToHost, s));
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, d_sync + 4, 4, cudaMemcpyDeviceToHost, s));
+    for (int i = 0; i < B; ++i) CK(cudaMemcpyAsync(&h_ctl[i], d_ctl[i], sizeof(InstCtl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+
+    if (h_err) return (sp2_status)h_err;
+    float ph[4] = {0.f, 0.f, 0.f, 0.f};
+    if (o.profile) {
+        CK(cudaEventElapsedTime(&ph[0], ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&ph[1], ev[1], ev[2]));
+        CK(cudaEventElapsedTime(&ph[2], ev[2], ev[3]));
+        CK(cudaEventElapsedTime(&ph[3], ev[0], ev[3]));
+    }
+    int worst = SP2_OK;
+    for (int i = 0; i < B; ++i) {
+        fill_stats(pl.inst[i].st, h_ctl[i]);
+        if (pl.inst[i].st)
+            for (int k = 0; k < 4; ++k) pl.inst[i].st->phase_ms[k] = ph[k];
+        int stt = h_ctl[i].status;
+        if (h_ctl[i].nonfinite) stt = SP2_ERR_NONFINITE;
+        if (status_rank(stt) > status_rank(worst)) worst = stt;
+    }
+    return (sp2_status)worst;
+}
+
+bool integral_occ(double n_occ, int n) {
+    return std::isfinite(n_occ) && n_occ >= 0.0 && n_occ <= (double)n && std::floor(n_occ) == n_occ;
+}
+
+sp2_status check_opts(const sp2_opts &o) {
+    if (o.precision < SP2_FP32_SIMT || o.precision > SP2_BF16_SPLIT) return SP2_ERR_ARG;
+    if (o.max_layers < 1 || o.max_layers > SP2_MAX_LAYERS_LIMIT) return SP2_ERR_ARG;
+    if (!(o.timeout_ms > 0.0)) return SP2_ERR_ARG;
+    if (o.user_bounds && !(o.eps_max > o.eps_min)) return SP2_ERR_ARG;
+    if (o.test_hook < 0 || o.test_hook > 1) return SP2_ERR_ARG;
+    if (o.profile < 0 || o.profile > 1) return SP2_ERR_ARG;
+    return SP2_OK;
+}
+
+// Trivial occupations: D = 0 or I, response and gradient 0.
+sp2_status run_trivial(const InstSpec &sp, cudaStream_t s) {
+    const size_t nn = (size_t)sp.n * sp.n;
+    const float diag = (sp.n_occ == 0.0) ? 0.0f : 1.0f;
+    auto fill = [&](float *p, float dv) -> sp2_status {
+        if (!p) return SP2_OK;
+        if (is_device_ptr(p)) {
+            if (launch_fill_trivial(p, sp.n, dv, s) != cudaSuccess) return SP2_ERR_CUDA;
+        } else {
+            if (cudaStreamSynchronize(s) != cudaSuccess) return SP2_ERR_CUDA;
+            for (size_t k = 0; k < nn; ++k) p[k] = ((k / sp.n) == (k % sp.n)) ? dv : 0.0f;
+        }
+        return SP2_OK;
+    };
+    sp2_status r = fill(sp.D, diag);
+    if (r != SP2_OK) return r;
+    r = fill(sp.D1, 0.0f);
+    if (r != SP2_OK) return r;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SP2_ERR_CUDA;
+    fill_trivial_stats(sp.st, sp.n, sp.n_occ);
+    if (sp.st && sp.H && sp.n_occ > 0.0) {
+        // Tr[I H] = sum of the diagonal, in FP64.
+        std::vector<double> diagv(sp.n);
+        double e = 0.0;
+        if (is_device_ptr(sp.H)) {
+            for (int i = 0; i < sp.n; ++i) {
+                if (cudaMemcpy(&diagv[i], sp.H + (size_t)i * sp.n + i, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return SP2_ERR_CUDA;
+            }
+        } else {
+            for (int i = 0; i < sp.n; ++i) diagv[i] = sp.H[(size_t)i * sp.n + i];
+        }
+        for (int i = 0; i < sp.n; ++i) e += diagv[i];
+        sp.st->band_energy = e;
+    }
+    return SP2_OK;
+}
+
+sp2_status run_instances(int mode, std::vector<InstSpec> &specs, double tol, const sp2_opts *opts, void *ws,
+                         size_t ws_bytes, void *stream) {
+    const sp2_opts o = resolve_opts(opts);
+    sp2_status r = check_opts(o);
+    if (r != SP2_OK) return r;
+    if (!(tol >= 0.0)) return SP2_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan pl;
+    pl.mode = mode;
+    pl.precision = o.precision;
+    pl.path = (o.precision == SP2_FP32_SIMT) ? PATH_SIMT : PATH_TC;
+    if ((mode == MODE_RESPONSE || mode == MODE_ADJOINT) && pl.path == PATH_SIMT) return SP2_ERR_UNSUPPORTED;
+    if ((int)specs.size() > MAX_BATCH) return SP2_ERR_ARG;
+    int worst = SP2_OK;
+    std::vector<int> order;
+    for (size_t k = 0; k < specs.size(); ++k) {
+        InstSpec &sp = specs[k];
+        if (sp.n < 1 || sp.n > 65536) return SP2_ERR_ARG;
+        if (!integral_occ(sp.n_occ, sp.n)) return SP2_ERR_ARG;
+        if (mode != MODE_APPLY && !sp.H) return SP2_ERR_ARG;
+        if ((mode == MODE_DENSITY || mode == MODE_APPLY) && !sp.D) return SP2_ERR_ARG;
+        if ((mode == MODE_RESPONSE || mode == MODE_ADJOINT) && (!sp.H1 || !sp.D1)) return SP2_ERR_ARG;
+        if (sp.fwd && (!sp.fwd->layer || sp.fwd->layer_cap < sp.fwd->layers + 1 || sp.fwd->layers < 0 ||
+                       sp.fwd->layers > SP2_MAX_LAYERS_LIMIT))
+            return SP2_ERR_ARG;
+        const bool trivial = (mode != MODE_APPLY) && (sp.n_occ == 0.0 || sp.n_occ == (double)sp.n);
+        if (trivial) {
+            sp2_status t = run_trivial(sp, s);
+            if (t != SP2_OK) return t;
+            continue;
+        }
+        order.push_back((int)k);
+    }
+    // Largest instances first: the static round-robin tile schedule then mixes
+    // long and short tiles across CTAs.
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return specs[a].n > specs[b].n; });
+    for (int k : order) {
+        const InstSpec &sp = specs[k];
+        pl.inst.push_back(sp);
+        int slots = 2;
+        if (mode == MODE_ADJOINT) slots = (sp.fwd ? sp.fwd->layers : o.max_layers) + 1;
+        pl.slots.push_back(slots);
+        pl.max_n = std::max(pl.max_n, sp.n);
+        pl.max_np = std::max(pl.max_np, round_up(sp.n, PAD));
+    }
+    r = run_plan(pl, tol, o, ws, ws_bytes, s);
+    if (status_rank(r) > status_rank(worst)) worst = r;
+    return (sp2_status)worst;
+}
+
+size_t bytes_for(int mode, const std::vector<int> &ns, int layers, const sp2_opts *opts) {
+    const sp2_opts o = resolve_opts(opts);
+    Plan pl;
+    pl.mode = mode;
+    pl.precision = o.precision;
+    pl.path = (o.precision == SP2_FP32_SIMT) ? PATH_SIMT : PATH_TC;
+    for (int n : ns) {
+        if (n < 1) continue;
+        InstSpec sp;
+        sp.n = n;
+        pl.inst.push_back(sp);
+        pl.slots.push_back(mode == MODE_ADJOINT ? (layers > 0 ? layers : o.max_layers) + 1 : 2);
+        pl.max_n = std::max(pl.max_n, n);
+        pl.max_np = std::max(pl.max_np, round_up(n, PAD));
+    }
+    if (pl.inst.empty()) return 0;
+    return plan_bytes(pl);
+}
+
+}  // namespace
+
+extern "C" {
+
+void sp2_default_opts(sp2_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = SP2_FP16_SPLIT;
+    o->max_layers = 100;
+    o->timeout_ms = 2000.0;
+    o->user_bounds = 0;
+}
+
+const char *sp2_status_string(sp2_status s) {
+    switch (s) {
+        case SP2_OK: return "ok";
+        case SP2_ERR_ARG: return "invalid argument";
+        case SP2_ERR_NONFINITE: return "non-finite input";
+        case SP2_ERR_NOT_CONVERGED: return "not converged within max_layers";
+        case SP2_ERR_TIMEOUT: return "device wait timed out";
+        case SP2_ERR_CUDA: return "CUDA error";
+        case SP2_ERR_NOMEM: return "out of memory";
+        case SP2_ERR_UNSUPPORTED: return "unsupported device or configuration";
+    }
+    return "unknown status";
+}
+
+sp2_status sp2_device_info(int *sm_count, int *cc_major, int *cc_minor) {
+    DeviceInfo di = query_device();
+    if (di.err != cudaSuccess) return SP2_ERR_CUDA;
+    if (sm_count) *sm_count = di.sm;
+    if (cc_major) *cc_major = di.major;
+    if (cc_minor) *cc_minor = di.minor;
+    return (di.major == 10 && di.minor == 3) ? SP2_OK : SP2_ERR_UNSUPPORTED;
+}
+
+size_t sp2_density_workspace_bytes(int N, const sp2_opts *o) { return bytes_for(MODE_DENSITY, {N}, 0, o); }
+
+size_t sp2_response_workspace_bytes(int N, const sp2_opts *o) { return bytes_for(MODE_RESPONSE, {N}, 0, o); }
+
+size_t sp2_adjoint_workspace_bytes(int N, int layers, const sp2_opts *o) {
+    return bytes_for(MODE_ADJOINT, {N}, layers, o);
+}
+
+size_t sp2_density_batched_workspace_bytes(int B, const int *N, const sp2_opts *o) {
+    if (B < 1 || !N) return 0;
+    return bytes_for(MODE_DENSITY, std::vector<int>(N, N + B), 0, o);
+}
+
+sp2_status sp2_density(const double *H, int N, double n_occ, double tol, float *D, sp2_stats *st, const sp2_opts *o,
+                       void *workspace, size_t ws_bytes, void *stream) {
+    std::vector<InstSpec> v(1);
+    v[0].n = N;
+    v[0].n_occ = n_occ;
+    v[0].H = H;
+    v[0].D = D;
+    v[0].st = st;
+    return run_instances(MODE_DENSITY, v, tol, o, workspace, ws_bytes, stream);
+}
+
+sp2_status sp2_response(const double *H, const double *H1, int N, double n_occ, double tol, const sp2_stats *fwd,
+                        float *D, float *D1, sp2_stats *st, const sp2_opts *o, void *workspace, size_t ws_bytes,
+                        void *stream) {
+    std::vector<InstSpec> v(1);
+    v[0].n = N;
+    v[0].n_occ = n_occ;
+    v[0].H = H;
+    v[0].H1 = H1;
+    v[0].D = D;
+    v[0].D1 = D1;
+    v[0].st = st;
+    v[0].fwd = fwd;
+    return run_instances(MODE_RESPONSE, v, tol, o, workspace, ws_bytes, stream);
+}
+
+sp2_status sp2_adjoint(const double *H, const double *G, int N, double n_occ, double tol, const sp2_stats *fwd,
+                       float *D, float *dH, sp2_stats *st, const sp2_opts *o, void *workspace, size_t ws_bytes,
+                       void *stream) {
+    std::vector<InstSpec> v(1);
+    v[0].n = N;
+    v[0].n_occ = n_occ;
+    v[0].H = H;
+    v[0].H1 = G;
+    v[0].D = D;
+    v[0].D1 = dH;
+    v[0].st = st;
+    v[0].fwd = fwd;
+    return run_instances(MODE_ADJOINT, v, tol, o, workspace, ws_bytes, stream);
+}
+
+sp2_status sp2_density_batched(int B, const double *const *H, const int *N, const double *n_occ, double tol,
+                               float *const *D, sp2_stats *st, const sp2_opts *o, void *workspace, size_t ws_bytes,
+                               void *stream) {
+    if (B < 1 || !H || !N || !n_occ || !D) return SP2_ERR_ARG;
+    std::vector<InstSpec> v(B);
+    for (int b = 0; b < B; ++b) {
+        v[b].n = N[b];
+        v[b].n_occ = n_occ[b];
+        v[b].H = H[b];
+        v[b].D = D[b];
+        v[b].st = st ? &st[b] : nullptr;
+    }
+    return run_instances(MODE_DENSITY, v, tol, o, workspace, ws_bytes, stream);
+}
+
+sp2_status sp2_apply_layers(const float *X0, int N, const int *choices, int n_layers, float *X, sp2_stats *st,
+                            const sp2_opts *o, void *stream) {
+    if (!X0 || !X || n_layers < 0 || n_layers > SP2_MAX_LAYERS_LIMIT || (n_layers > 0 && !choices))
+        return SP2_ERR_ARG;
+    for (int k = 0; k < n_layers; ++k)
+        if (choices[k] != SP2_CHOICE_SQUARE && choices[k] != SP2_CHOICE_FLIP) return SP2_ERR_ARG;
+    std::vector<InstSpec> v(1);
+    v[0].n = N;
+    v[0].n_occ = 0.0;
+    v[0].X0 = X0;
+    v[0].D = X;
+    v[0].st = st;
+    v[0].choices = choices;
+    v[0].nchoices = n_layers;
+    return run_instances(MODE_APPLY, v, 1e300, o, nullptr, 0, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,381 @@
+// aux_kernels.cu -- the HBM-bound steps around the layer loop:
+//   * Gershgorin spectral bounds of H in FP64 (one read pass over H),
+//   * the input layer X_0 = (eps_max I - H)/(eps_max - eps_min) with its FP32
+//     master, split operands and FP64 trace partials (one read of H, one write of X),
+//   * the response / adjoint stream start Y_0 (scaled by a power of two),
+//   * the output copy D = X_L with FP64 Tr[D H] and Tr D.
+#include "device_common.cuh"
+
+namespace sp2i {
+
+namespace {
+
+constexpr int AUX_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+    // Fixed shuffle-down tree: lane 0 holds the sum, in the same order every run.
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide deterministic sum of three doubles; result valid in thread 0.
+__device__ __forceinline__ double3 block_sum3(double a, double b, double c) {
+    __shared__ double sa[AUX_THREADS / 32], sb[AUX_THREADS / 32], sc[AUX_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    c = warp_sum_d(c);
+    if (lane == 0) {
+        sa[w] = a;
+        sb[w] = b;
+        sc[w] = c;
+    }
+    __syncthreads();
+    double3 r = make_double3(0.0, 0.0, 0.0);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < AUX_THREADS / 32; ++k) {
+            r.x += sa[k];
+            r.y += sb[k];
+            r.z += sc[k];
+        }
+    }
+    __syncthreads();
+    return r;
+}
+
+// Block-wide deterministic sum of two doubles; result valid in thread 0.
+__device__ __forceinline__ double2 block_sum2(double a, double b) {
+    __shared__ double sa[AUX_THREADS / 32], sb[AUX_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (lane == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < AUX_THREADS / 32; ++k) {
+            r.x += sa[k];
+            r.y += sb[k];
+        }
+    }
+    __syncthreads();
+    return r;
+}
+
+// Gershgorin discs: one warp per row, FP64 row sums of |H_ij|, j != i.
+__global__ void __launch_bounds__(AUX_THREADS) k_gershgorin(InstDesc *inst) {
+    const InstDesc &d = inst[blockIdx.y];
+    const int n = d.n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double lo = INFINITY, hi = -INFINITY;
+    int bad = 0;
+    for (int row = blockIdx.x * (AUX_THREADS / 32) + w; row < n; row += gridDim.x * (AUX_THREADS / 32)) {
+        const double *h = d.H + (size_t)row * n;
+        double r0 = 0.0, r1 = 0.0;
+        int j = lane;
+        for (; j + 32 < n; j += 64) {
+            double v0 = h[j], v1 = h[j + 32];
+            bad |= !isfinite(v0) | !isfinite(v1);
+            r0 += (j == row) ? 0.0 : fabs(v0);
+            r1 += (j + 32 == row) ? 0.0 : fabs(v1);
+        }
+        if (j < n) {
+            double v0 = h[j];
+            bad |= !isfinite(v0);
+            r0 += (j == row) ? 0.0 : fabs(v0);
+        }
+        double r = warp_sum_d(r0 + r1);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        const double dv = h[row];
+        lo = fmin(lo, dv - r);
+        hi = fmax(hi, dv + r);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        if (lo <= hi) {
+            atomicMin(&d.ctl->emin_key, dkey(lo));
+            atomicMax(&d.ctl->emax_key, dkey(hi));
+        }
+        if (bad) atomicOr(&d.ctl->nonfinite, 1);
+    }
+}
+
+// max |M_ij| over an n x n FP64 matrix (H1 or G), for the power-of-two scale of Y.
+__global__ void __launch_bounds__(AUX_THREADS) k_maxabs(InstDesc *inst) {
+    const InstDesc &d = inst[blockIdx.y];
+    const size_t total = (size_t)d.n * d.n;
+    double m = 0.0;
+    int bad = 0;
+    for (size_t e = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; e < total; e += (size_t)gridDim.x * AUX_THREADS) {
+        double v = d.H1[e];
+        bad |= !isfinite(v);
+        m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&d.ctl->ymax_key, dkey(m));
+        if (bad) atomicOr(&d.ctl->nonfinite, 1);
+    }
+}
+
+__device__ __forceinline__ void resolve_bounds(const InstDesc &d, bool user_bounds, double &emin, double &emax) {
+    if (user_bounds) {
+        emin = d.ctl->eps_min;
+        emax = d.ctl->eps_max;
+    } else {
+        emin = dkey_value(d.ctl->emin_key);
+        emax = dkey_value(d.ctl->emax_key);
+    }
+}
+
+// X_0 over the padded np x np matrix; four consecutive columns per thread.
+template <int PATH, int PREC>
+__global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user_bounds) {
+    const InstDesc &d = inst[blockIdx.y];
+    const int n = d.n, np = d.np;
+    double emin, emax;
+    resolve_bounds(d, user_bounds != 0, emin, emax);
+    const double delta = emax - emin;
+    const bool degenerate = !(delta > 0.0) || !isfinite(delta) || d.ctl->nonfinite;
+    const double inv = degenerate ? 0.0 : 1.0 / delta;
+    float *xf = d.xf[0];
+    uint16_t *op0 = d.xop, *op1 = d.xop + (size_t)np * np, *op2 = d.xop + 2 * (size_t)np * np;
+    FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
+    const size_t total4 = (size_t)np * np / 4;
+    for (size_t e4 = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; e4 < total4; e4 += (size_t)gridDim.x * AUX_THREADS) {
+        const size_t idx = e4 * 4;
+        const int i = (int)(idx / np), j0 = (int)(idx % np);
+        float x[4], y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            float v = 0.0f;
+            if (i < n && j < n) {
+                const double h = d.H[(size_t)i * n + j];
+                v = (float)((((i == j) ? emax : 0.0) - h) * inv);
+            }
+            x[q] = v;
+            y[q] = (i == j && i < n) ? v - 0.5f : v;
+            if (i == j) ff_add(ft, v);
+            ff_add_sq(fq, v, 1.0f);
+            if (PATH == PATH_TC) ff_add_sq(fw, y[q], 1.0f);
+        }
+        *(float4 *)(xf + idx) = make_float4(x[0], x[1], x[2], x[3]);
+        if (PATH == PATH_TC) {
+            // operands of the first square: the split of Y_0 = X_0 - I/2
+            uint16_t a[4], b[4], c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split3<PREC>(y[q], a[q], b[q], c[q]);
+            if (PREC == SP2_FP16_SPLIT) *(ushort4 *)(op0 + idx) = make_ushort4(a[0], a[1], a[2], a[3]);
+            *(ushort4 *)(op1 + idx) = make_ushort4(b[0], b[1], b[2], b[3]);
+            *(ushort4 *)(op2 + idx) = make_ushort4(c[0], c[1], c[2], c[3]);
+        }
+    }
+    double3 s = block_sum3(ff_value(ft), ff_value(fq), ff_value(fw));
+    if (threadIdx.x == 0) {
+        Part pr;
+        pr.t = s.x;
+        pr.q = s.y;
+        pr.w = s.z;
+        pr.p = 0.0;
+        d.part[0][blockIdx.x] = pr;
+        if (blockIdx.x == 0) {
+            d.ctl->init_parts = gridDim.x;
+            d.ctl->eps_min = emin;
+            d.ctl->eps_max = emax;
+            if (d.ctl->nonfinite) d.ctl->status = SP2_ERR_NONFINITE;
+            else if (degenerate) d.ctl->degenerate = 1;
+        }
+    }
+}
+
+// X_0 given directly (FP32, n x n), for the layer-application entry point.
+template <int PATH, int PREC>
+__global__ void __launch_bounds__(AUX_THREADS) k_init_x_from(InstDesc *inst, const float *X0) {
+    const InstDesc &d = inst[0];
+    const int n = d.n, np = d.np;
+    float *xf = d.xf[0];
+    uint16_t *op0 = d.xop, *op1 = d.xop + (size_t)np * np, *op2 = d.xop + 2 * (size_t)np * np;
+    FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
+    const size_t total = (size_t)np * np;
+    for (size_t idx = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; idx < total; idx += (size_t)gridDim.x * AUX_THREADS) {
+        const int i = (int)(idx / np), j = (int)(idx % np);
+        const float v = (i < n && j < n) ? X0[(size_t)i * n + j] : 0.0f;
+        xf[idx] = v;
+        if (i == j) ff_add(ft, v);
+        ff_add_sq(fq, v, 1.0f);
+        if (PATH == PATH_TC) {
+            const float y = (i == j && i < n) ? v - 0.5f : v;
+            ff_add_sq(fw, y, 1.0f);
+            uint16_t a, b, c;
+            split3<PREC>(y, a, b, c);
+            if (PREC == SP2_FP16_SPLIT) op0[idx] = a;
+            op1[idx] = b;
+            op2[idx] = c;
+        }
+    }
+    double3 s = block_sum3(ff_value(ft), ff_value(fq), ff_value(fw));
+    if (threadIdx.x == 0) {
+        Part pr;
+        pr.t = s.x;
+        pr.q = s.y;
+        pr.w = s.z;
+        pr.p = 0.0;
+        d.part[0][blockIdx.x] = pr;
+        if (blockIdx.x == 0) d.ctl->init_parts = gridDim.x;
+    }
+}
+
+// Y_0 = coef * y_scale * (M + M^T)/2 over the padded matrix.  coef is
+// -1/(eps_max - eps_min) for the response (X1_0 = -H1/(eps_max - eps_min)) and 1
+// for the adjoint (G_L = sym(G)); y_scale is the power of two that brings
+// max |Y_0| into (1/2, 1] so that the 16-bit split operands stay in range.
+template <int PREC>
+__global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode) {
+    const InstDesc &d = inst[0];
+    const int n = d.n, np = d.np;
+    const double emin = d.ctl->eps_min, emax = d.ctl->eps_max;
+    const double coef = (mode == MODE_RESPONSE) ? -1.0 / (emax - emin) : 1.0;
+    const double mabs = dkey_value(d.ctl->ymax_key) * fabs(coef);
+    int ex = 0;
+    if (mabs > 0.0 && isfinite(mabs)) frexp(mabs, &ex);  // mabs in [2^(ex-1), 2^ex)
+    const double yscale = ldexp(1.0, -ex);
+    const double c = coef * yscale;
+    uint16_t *op1 = d.yop + (size_t)np * np, *op2 = d.yop + 2 * (size_t)np * np;
+    const size_t total = (size_t)np * np;
+    for (size_t idx = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; idx < total; idx += (size_t)gridDim.x * AUX_THREADS) {
+        const int i = (int)(idx / np), j = (int)(idx % np);
+        double a = 0.0, b = 0.0;
+        if (i < n && j < n) {
+            a = d.H1[(size_t)i * n + j];
+            b = d.H1[(size_t)j * n + i];
+        }
+        const float y = (float)(0.5 * (a + b) * c);
+        d.yf[0][idx] = y;
+        uint16_t o0, o1, o2;
+        split3<PREC>(y, o0, o1, o2);
+        op1[idx] = o1;
+        op2[idx] = o2;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.ctl->y_scale = yscale;
+}
+
+// D = X_L (un-padded copy), partial FP64 sums of D_ij H_ij and D_ii per block;
+// the response / adjoint output is the Y stream with its scale removed.
+__global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mode) {
+    const InstDesc &d = inst[blockIdx.y];
+    if (blockIdx.x >= d.fin_blocks) return;
+    const int n = d.n, np = d.np;
+    const InstCtl *ctl = d.ctl;
+    const float *X = d.xf[ctl->final_x & 1];
+    const float *Y = d.yf[ctl->final_y & 1];
+    const float xoff = (float)ctl->x_offset;
+    float ys = 0.0f;
+    if (mode == MODE_RESPONSE) ys = (float)(1.0 / ctl->y_scale);
+    if (mode == MODE_ADJOINT) ys = (float)(-1.0 / (ctl->y_scale * (ctl->eps_max - ctl->eps_min)));
+    double e = 0.0, tr = 0.0;
+    const size_t total = (size_t)n * n;
+    for (size_t idx = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; idx < total; idx += (size_t)d.fin_blocks * AUX_THREADS) {
+        const int i = (int)(idx / n), j = (int)(idx % n);
+        float x = X[(size_t)i * np + j];
+        if (i == j) x += xoff;  // true X_L = stored X_L + c_L I
+        if (d.out) d.out[idx] = x;
+        if (d.H) e += (double)x * d.H[idx];
+        if (i == j) tr += x;
+        if (mode == MODE_RESPONSE || mode == MODE_ADJOINT) d.out1[idx] = Y[(size_t)i * np + j] * ys;
+    }
+    double2 s = block_sum2(e, tr);
+    if (threadIdx.x == 0) d.fin_part[blockIdx.x] = s;
+}
+
+__global__ void k_finalize_reduce(InstDesc *inst) {
+    const InstDesc &d = inst[blockIdx.x];
+    if (threadIdx.x != 0) return;
+    double e = 0.0, tr = 0.0;
+    for (int k = 0; k < d.fin_blocks; ++k) {
+        e += d.fin_part[k].x;
+        tr += d.fin_part[k].y;
+    }
+    d.ctl->band_energy = e;
+    d.ctl->trace_D = tr;
+}
+
+__global__ void k_fill_trivial(float *D, int n, float diag) {
+    const size_t total = (size_t)n * n;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x)
+        D[idx] = ((idx / n) == (idx % n)) ? diag : 0.0f;
+}
+
+int grid_for(size_t work, int per_block, int cap) {
+    size_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > (size_t)cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_gershgorin(InstDesc *inst, int B, int max_n, bool user_bounds, cudaStream_t s) {
+    (void)user_bounds;  // bounds are computed anyway: the same pass detects non-finite input
+    dim3 grid(grid_for((size_t)max_n, AUX_THREADS / 32, 2048), B);
+    k_gershgorin<<<grid, AUX_THREADS, 0, s>>>(inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs(InstDesc *inst, int B, int max_n, cudaStream_t s) {
+    dim3 grid(grid_for((size_t)max_n * max_n, AUX_THREADS * 8, 2048), B);
+    k_maxabs<<<grid, AUX_THREADS, 0, s>>>(inst);
+    return cudaGetLastError();
+}
+
+int init_blocks_for(int np) { return grid_for((size_t)np * np / 4, AUX_THREADS * 8, INIT_BLOCKS_MAX); }
+
+cudaError_t launch_init_x(InstDesc *inst, int B, int max_np, int path, int precision, bool user_bounds,
+                          cudaStream_t s) {
+    dim3 grid(init_blocks_for(max_np), B);
+    // Every instance must be covered by the same number of blocks it reports in
+    // init_parts: the grid-stride loop handles any np with this grid.
+    const int ub = user_bounds ? 1 : 0;
+    if (path == PATH_SIMT) k_init_x<PATH_SIMT, SP2_FP16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, ub);
+    else if (precision == SP2_BF16_SPLIT) k_init_x<PATH_TC, SP2_BF16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, ub);
+    else k_init_x<PATH_TC, SP2_FP16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, ub);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_x_from(InstDesc *inst, const float *X0, int np, int path, int precision, cudaStream_t s) {
+    // Same block count rule as the input layer: the partial buffer holds
+    // max(tiles, init_blocks_for(np)) entries and every block writes one.
+    const int grid = init_blocks_for(np);
+    if (path == PATH_SIMT) k_init_x_from<PATH_SIMT, SP2_FP16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, X0);
+    else if (precision == SP2_BF16_SPLIT) k_init_x_from<PATH_TC, SP2_BF16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, X0);
+    else k_init_x_from<PATH_TC, SP2_FP16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, X0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_y(InstDesc *inst, int mode, int precision, cudaStream_t s) {
+    const int grid = 1024;
+    if (precision == SP2_BF16_SPLIT) k_init_y<SP2_BF16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, mode);
+    else k_init_y<SP2_FP16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(InstDesc *inst, int B, int max_n, int mode, cudaStream_t s) {
+    (void)max_n;
+    dim3 grid(FIN_BLOCKS_MAX, B);
+    k_finalize<<<grid, AUX_THREADS, 0, s>>>(inst, mode);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_finalize_reduce<<<B, 32, 0, s>>>(inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_trivial(float *D, int n, float diag_value, cudaStream_t s) {
+    k_fill_trivial<<<grid_for((size_t)n * n, 256, 4096), 256, 0, s>>>(D, n, diag_value);
+    return cudaGetLastError();
+}
+
+}  // namespace sp2i

@@ -1,0 +1,347 @@
+// device_common.cuh -- device helpers shared by the SP2 kernels:
+// compensated FP32 accumulation, order-preserving double keys, the hi/lo
+// operand split, the grid barrier with a time limit, and the per-round layer
+// decision (trace-correcting sign, idempotency stop rule) taken on the device.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "sp2_internal.h"
+
+namespace sp2i {
+
+// ---------------------------------------------------------------------------
+// Compensated (two-float) accumulation.  Each product x*x of an FP32 value is
+// split exactly into p + e with an FMA; the running sum keeps its rounding
+// error in a second float (TwoSum).  The pair carries ~48 significant bits,
+// enough for the idempotency estimate Tr X - ||X||_F^2 at any size used here,
+// at FP32 throughput (GB300 issues FP64 at a small fraction of FP32).
+// The __f*_rn intrinsics keep the compiler from contracting the sums into FMAs.
+// ---------------------------------------------------------------------------
+struct FF {
+    float s, c;
+};
+
+__device__ __forceinline__ void ff_add(FF &a, float v) {
+    float t = __fadd_rn(a.s, v);
+    float bp = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+}
+
+// a += w * x * x, w in {1, 2} (exact scaling by 2)
+__device__ __forceinline__ void ff_add_sq(FF &a, float x, float w) {
+    float p = __fmul_rn(x, x);
+    float e = __fmaf_rn(x, x, -p);
+    ff_add(a, __fmul_rn(w, p));
+    a.c = __fadd_rn(a.c, __fmul_rn(w, e));
+}
+
+__device__ __forceinline__ double ff_value(const FF &a) { return (double)a.s + (double)a.c; }
+
+// ---------------------------------------------------------------------------
+// Order-preserving 64-bit keys so that min / max of doubles can use integer
+// atomics (exact and independent of arrival order).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long dkey(double v) {
+    unsigned long long b;
+#ifdef __CUDA_ARCH__
+    b = (unsigned long long)__double_as_longlong(v);
+#else
+    memcpy(&b, &v, 8);
+#endif
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ __forceinline__ double dkey_value(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double v;
+    memcpy(&v, &b, 8);
+    return v;
+#endif
+}
+
+// ---------------------------------------------------------------------------
+// The split X = X^(0) + X^(1) (section "Deep-neural network electronic structure
+// solver", the dual matrix representation), with round-to-nearest-even.
+// FP16: op1 = hi = FP16[x]; op2 = FP16[(x - hi) * 2^11]; op0 = hi * 2^11 (exact).
+//   lo is kept scaled so that it stays in FP16's normal range; every product in
+//   the K-loop then carries the same factor 2^11, removed in the epilogue.
+// BF16: op1 = op0 = hi = BF16[x]; op2 = BF16[x - hi] (no range problem).
+// x - hi is exact in FP32 in both cases.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_fp16(float x, uint16_t &o0, uint16_t &o1, uint16_t &o2) {
+    __half h = __float2half_rn(x);
+    float hf = __half2float(h);
+    o1 = __half_as_ushort(h);
+    o0 = __half_as_ushort(__float2half_rn(hf * (float)(1 << LO_SHIFT)));
+    o2 = __half_as_ushort(__float2half_rn(__fsub_rn(x, hf) * (float)(1 << LO_SHIFT)));
+}
+__device__ __forceinline__ void split_bf16(float x, uint16_t &o0, uint16_t &o1, uint16_t &o2) {
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    float hf = __bfloat162float(h);
+    o1 = __bfloat16_as_ushort(h);
+    o0 = o1;
+    o2 = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(x, hf)));
+}
+template <int PREC>
+__device__ __forceinline__ void split3(float x, uint16_t &o0, uint16_t &o1, uint16_t &o2) {
+    if (PREC == SP2_FP16_SPLIT) split_fp16(x, o0, o1, o2);
+    else split_bf16(x, o0, o1, o2);
+}
+template <int PREC>
+__host__ __device__ __forceinline__ float split_unscale() {
+    return PREC == SP2_FP16_SPLIT ? 1.0f / (float)(1 << LO_SHIFT) : 1.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Timers and memory-order helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+__device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }
+
+// Grid barrier for a cooperative (co-resident) launch: every CTA's thread 0
+// adds one arrival and waits until `target` arrivals are counted.  Gives up
+// after `timeout_ns` (or when another CTA reported an error) and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int target, int *err,
+                                             unsigned long long timeout_ns, bool withhold = false) {
+    __threadfence();
+    if (!withhold) atomicAdd(counter, 1u);
+    unsigned long long t0 = global_ns();
+    while (ld_acquire(counter) < target) {
+        if (ld_volatile(err) != 0) return false;
+        if (global_ns() - t0 > timeout_ns) {
+            set_error(err, SP2_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Per-round control state kept in shared memory by every CTA.  Every CTA
+// computes the same decisions from the same FP64 partials in the same order,
+// so no broadcast between CTAs is needed; CTA 0 alone writes the statistics.
+// ---------------------------------------------------------------------------
+struct RoundCtl {
+    int abort;
+    int total;                       // tiles in this round over all instances
+    int phase;                       // adjoint: 0 forward, 1 reverse
+    int rev_left;                    // adjoint: reverse layers still to do
+    int rev_total;                   // adjoint: forward layer count L
+    int prefix[MAX_BATCH + 1];       // active tile prefix over instances
+    int layer[MAX_BATCH];            // index n of the current X_n
+    int jobs[MAX_BATCH];             // 0 (inactive), 1 (square) or 2 (square + response)
+    signed char choice[MAX_BATCH];   // sign of the layer computed this round
+    unsigned char active[MAX_BATCH];
+    unsigned char ran[MAX_BATCH];    // instance computed a layer in the previous round
+    double ehist[MAX_BATCH][2];
+    double wprev[MAX_BATCH];         // ||Y_n||_F^2 of the operands of the current square
+    double coff[MAX_BATCH];          // c_n: true X_n = stored X_n + c_n I
+    signed char chist[MAX_L + 2];    // adjoint (B = 1): choice that produced X_n
+    double chist_c[MAX_L + 2];       // adjoint (B = 1): c_n per layer
+};
+
+__device__ __forceinline__ int layer_rule(double t, double q, double n_occ) {
+    return fabs(q - n_occ) <= fabs(2.0 * t - q - n_occ) ? SP2_CHOICE_SQUARE : SP2_CHOICE_FLIP;
+}
+
+__device__ __forceinline__ void round_ctl_init(RoundCtl &rc, const RunParams &p) {
+    rc.abort = 0;
+    rc.total = 0;
+    rc.phase = 0;
+    rc.rev_left = 0;
+    rc.rev_total = 0;
+    for (int i = 0; i < p.B; ++i) {
+        InstCtl *ctl = p.inst[i].ctl;
+        rc.layer[i] = 0;
+        rc.jobs[i] = 0;
+        rc.choice[i] = SP2_CHOICE_INPUT;
+        rc.active[i] = (ctl->status == 0) ? 1 : 0;
+        rc.ran[i] = 0;
+        rc.ehist[i][0] = rc.ehist[i][1] = 0.0;
+        rc.wprev[i] = 0.0;
+        rc.coff[i] = 0.0;
+    }
+    rc.chist[0] = SP2_CHOICE_INPUT;
+}
+
+// Thread 0 of every CTA: reduce the partials of the layer just finished,
+// record statistics (CTA 0), apply the stop rule and pick the next signs.
+__device__ inline void decide_round(RoundCtl &rc, const RunParams &p) {
+    const bool writer = (blockIdx.x == 0);
+    if (ld_volatile(p.err) != 0) {
+        rc.abort = 1;
+        return;
+    }
+    if (rc.phase == 1) {  // adjoint reverse sweep (B == 1); layer[0] counts reverse rounds done
+        rc.layer[0] += 1;
+        rc.rev_left -= 1;
+        rc.prefix[0] = 0;
+        if (rc.rev_left <= 0) {
+            if (writer) p.inst[0].ctl->final_y = rc.layer[0] & 1;  // Y buffer holding G_0
+            rc.prefix[1] = 0;
+            rc.total = 0;
+            return;
+        }
+        rc.jobs[0] = 1;
+        rc.prefix[1] = p.inst[0].ntiles;
+        rc.total = p.inst[0].ntiles;
+        return;
+    }
+    int acc = 0;
+    rc.prefix[0] = 0;
+    for (int i = 0; i < p.B; ++i) {
+        const InstDesc &d = p.inst[i];
+        InstCtl *ctl = d.ctl;
+        int width = 0;
+        if (rc.active[i]) {
+            if (rc.ran[i]) rc.layer[i] += 1;
+            const int n = rc.layer[i];
+            const int cnt = (n == 0) ? ctl->init_parts : d.ntiles;
+            const Part *part = d.part[n & 1];
+            double ts = 0.0, qs = 0.0, ws = 0.0, ps = 0.0;
+            for (int k = 0; k < cnt; ++k) {
+                const Part v = part[k];
+                ts += v.t;
+                qs += v.q;
+                ws += v.w;
+                ps += v.p;
+            }
+            const int made = (n == 0) ? SP2_CHOICE_INPUT : rc.choice[i];
+            // Accumulator bias of the square that made X_n: in exact arithmetic
+            // Tr(Y^2) = ||Y||_F^2 for the symmetric operand Y, so the deficit of the
+            // computed trace, spread over the N diagonal entries, is the identity
+            // component of the product error.  It is removed as the offset c_n of
+            // X_n (sign of the layer: X^2 keeps it, 2X - X^2 negates it).  Both
+            // sums are zero on the FP32 path, where c_n stays 0.
+            double c = 0.0;
+            if (n > 0) {
+                const double gam = (rc.wprev[i] - ps) / (double)d.n;
+                c = (made == SP2_CHOICE_SQUARE) ? gam : -gam;
+            }
+            const double t = ts + (double)d.n * c;
+            const double q = qs + 2.0 * c * ts + (double)d.n * c * c;
+            rc.wprev[i] = ws;
+            rc.coff[i] = c;
+            rc.chist_c[n] = c;
+            if (writer) {
+                LayerStatDev st;
+                st.trace = t;
+                st.trace_sq = q;
+                st.idem = t - q;
+                st.choice = made;
+                st.reserved = 0;
+                ctl->stat[n] = st;
+            }
+            rc.chist[n] = (signed char)made;
+            const double e = fabs(t - q);
+            const double e2 = rc.ehist[i][n & 1];
+            rc.ehist[i][n & 1] = e;
+            int reason = 0, status = 0;
+            bool stop = false;
+            if (!isfinite(t) || !isfinite(q)) {
+                stop = true;
+                status = SP2_ERR_NONFINITE;
+            } else if (ctl->degenerate) {
+                stop = true;
+                status = SP2_ERR_NOT_CONVERGED;
+                reason = SP2_STOP_MAX;
+            } else if (d.nforced >= 0) {
+                if (n >= d.nforced) {
+                    stop = true;
+                    if (e <= p.tol) reason = SP2_STOP_TOL;
+                    else if (n >= 2 && e <= STALL_MAX && e >= e2) reason = SP2_STOP_STALL;
+                    else reason = SP2_STOP_NONE;
+                }
+            } else if (e <= p.tol) {
+                stop = true;
+                reason = SP2_STOP_TOL;
+            } else if (n >= 2 && e <= STALL_MAX && e >= e2) {
+                stop = true;
+                reason = SP2_STOP_STALL;
+            } else if (n >= p.max_layers) {
+                stop = true;
+                reason = SP2_STOP_MAX;
+                status = SP2_ERR_NOT_CONVERGED;
+            }
+            if (stop) {
+                rc.active[i] = 0;
+                rc.ran[i] = 0;
+                if (writer) {
+                    ctl->layers = n;
+                    ctl->stop_reason = reason;
+                    ctl->status = status;
+                    ctl->final_x = n & 1;
+                    ctl->final_y = n & 1;
+                    ctl->x_offset = c;
+                }
+                if (p.mode == MODE_ADJOINT && status == 0) {
+                    // Switch to the reverse sweep: G_L is in Y buffer 0.  Reverse round
+                    // k (= layer[0]) maps G_{m+1} to G_m with m = L - 1 - k, reading Y
+                    // buffer k & 1 and X_m from slot m.
+                    rc.phase = 1;
+                    rc.rev_total = n;
+                    rc.rev_left = n;
+                    rc.layer[0] = 0;
+                    rc.prefix[1] = 0;
+                    rc.total = 0;
+                    if (n == 0) {
+                        if (writer) ctl->final_y = 0;
+                        return;
+                    }
+                    rc.jobs[0] = 1;
+                    rc.prefix[1] = d.ntiles;
+                    rc.total = d.ntiles;
+                    return;
+                }
+            } else {
+                const int c = (d.nforced >= 0) ? d.forced[n] : layer_rule(t, q, d.n_occ);
+                rc.choice[i] = (signed char)c;
+                rc.ran[i] = 1;
+                rc.jobs[i] = (p.mode == MODE_RESPONSE) ? 2 : 1;
+                width = rc.jobs[i] * d.ntiles;
+            }
+        }
+        if (!rc.active[i]) rc.jobs[i] = 0;
+        acc += width;
+        rc.prefix[i + 1] = acc;
+    }
+    rc.total = acc;
+}
+
+// Map a round-global tile index to (instance, job, tile).
+__device__ __forceinline__ void map_tile(const RoundCtl &rc, int B, const InstDesc *inst, int g, int &i,
+                                         int &job, int &tile) {
+    int lo = 0, hi = B;  // find i with prefix[i] <= g < prefix[i+1]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (rc.prefix[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    i = lo;
+    int local = g - rc.prefix[i];
+    int nt = inst[i].ntiles;
+    job = local / nt;
+    tile = local - job * nt;
+}
+
+}  // namespace sp2i

@@ -1,0 +1,120 @@
+// sp2_internal.h -- data layout shared by the host launcher and the device kernels.
+//
+// Device memory per instance (all row-major, padded size np = round_up(N, 128)):
+//   xf[2]       FP32 master copy of X_n, ping-pong by layer parity.
+//   xop slots   split operands of X_n, three 16-bit matrices per slot
+//               (FP16: hi * 2^11, hi, lo * 2^11;  BF16: hi, hi, lo), so that the
+//               square is one K-loop of length 3*np over A = [op0 | op1 | op2] and
+//               B = [op1 | op2 | op1] (Eq. activ: A + B + B^T with the lo*lo term
+//               dropped, all three products in one FP32 accumulator).
+//   yf[2], yop  the response / adjoint stream (FP32 master + ops 1, 2).
+//   part[2]     FP64 partials per tile, ping-pong by layer parity: Tr X, ||X||_F^2,
+//               ||Y||_F^2 and Tr P (see Part).
+// Tensor-core path: the operands are the split of Y = X - I/2 (identity on the
+// first N diagonal entries only), and the true X_n is the stored FP32 X_n plus
+// c_n I, where the scalar c_n removes the measured accumulator bias of the
+// previous square (see the tensor-core kernel).
+// Padding lives in X space: rows and columns N..np-1 of X_0 are zero, and zero
+// rows and columns stay zero under both X^2 and 2X - X^2.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sp2.h"
+
+namespace sp2i {
+
+constexpr int PAD = 128;            // np is a multiple of this
+constexpr int TC_BM = 128;          // tcgen05 tile rows (UMMA M)
+constexpr int TC_BN = 256;          // tcgen05 tile columns (UMMA N)
+constexpr int TC_BK = 64;           // K block: 64 x 16-bit = one 128-byte swizzle row
+constexpr int TC_STAGES = 4;        // TMA -> MMA pipeline depth
+constexpr int TC_THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int SIMT_T = 128;         // FP32 SIMT tile (square)
+constexpr int SIMT_THREADS = 256;
+constexpr int MAX_BATCH = 128;
+constexpr int MAX_L = SP2_MAX_LAYERS_LIMIT;
+constexpr int INIT_BLOCKS_MAX = 512;
+constexpr int FIN_BLOCKS_MAX = 256;
+constexpr int LO_SHIFT = 11;        // FP16 lo parts are stored times 2^11 (exact scaling)
+constexpr double STALL_MAX = 1e-2;
+
+enum Path { PATH_SIMT = 0, PATH_TC = 1 };
+enum Mode { MODE_DENSITY = 0, MODE_RESPONSE = 1, MODE_ADJOINT = 2, MODE_APPLY = 3 };
+
+// Per-tile FP64 partial sums written by the input layer and every square.
+struct __align__(16) Part {
+    double t;   // Tr X (stored X)
+    double q;   // ||X||_F^2 (stored X)
+    double w;   // ||Y||_F^2 of the split operand matrix Y the next square multiplies (0 on the FP32 path)
+    double p;   // Tr P, P the raw product of this square (0 on the FP32 path)
+};
+
+struct LayerStatDev {
+    double trace, trace_sq, idem;
+    int choice, reserved;
+};
+
+struct InstCtl {
+    double eps_min, eps_max, band_energy, trace_D;
+    double y_scale;                          // power of two applied to the Y stream
+    double x_offset;                         // c_L: D = stored X_L + c_L I
+    unsigned long long emin_key, emax_key;   // order-preserving keys for atomic min / max
+    unsigned long long ymax_key;
+    int nonfinite, status, layers, stop_reason;
+    int final_x, final_y, init_parts, degenerate;
+    LayerStatDev stat[MAX_L + 1];
+};
+
+struct InstDesc {
+    int n, np, ntiles, tile_off;      // tiles: this instance's slice of the tile table
+    double n_occ;
+    int nforced, nslots_x;            // nforced < 0: decide on device; nslots_x: 2 or L+1
+    const int *forced;                // replayed layer choices (device)
+    float *xf[2];
+    uint16_t *xop;                    // slot s, op k at xop + (s*3 + k) * np * np
+    float *yf[2];
+    uint16_t *yop;                    // slot s in {0,1}, op k
+    Part *part[2];
+    int part_cap, fin_blocks;
+    const CUtensorMap *xmap;          // [nslots_x * 3]
+    const CUtensorMap *ymap;          // [2 * 3]
+    const double *H;                  // device copy of H (n x n)
+    const double *H1;                 // response perturbation or adjoint weight (n x n)
+    float *out;                       // D (n x n)
+    float *out1;                      // D1 or dH (n x n)
+    double2 *fin_part;                // finalisation partials
+    InstCtl *ctl;
+};
+
+struct RunParams {
+    InstDesc *inst;
+    const int2 *tiles;                // (bi, bj) per tile, per instance slice
+    unsigned int *barrier;            // grid barrier arrival counter (zeroed per launch)
+    int *err;                         // first fatal device error (SP2_ERR_*), 0 = none
+    double tol;
+    unsigned long long timeout_ns;
+    int B, mode, precision, max_layers;
+    int test_hook;                    // 1: CTA 0 withholds its first barrier arrival
+};
+
+// Host-side launchers (one translation unit each).
+cudaError_t launch_gershgorin(InstDesc *inst, int B, int max_n, bool user_bounds, cudaStream_t s);
+cudaError_t launch_maxabs(InstDesc *inst, int B, int max_n, cudaStream_t s);
+cudaError_t launch_init_x(InstDesc *inst, int B, int max_np, int path, int precision, bool user_bounds,
+                          cudaStream_t s);
+cudaError_t launch_init_x_from(InstDesc *inst, const float *X0, int np, int path, int precision, cudaStream_t s);
+cudaError_t launch_init_y(InstDesc *inst, int mode, int precision, cudaStream_t s);
+cudaError_t launch_finalize(InstDesc *inst, int B, int max_n, int mode, cudaStream_t s);
+cudaError_t launch_fill_trivial(float *D, int n, float diag_value, cudaStream_t s);
+cudaError_t launch_simt_persistent(const RunParams &p, int grid, cudaStream_t s);
+cudaError_t launch_tc_persistent(const RunParams &p, int grid, cudaStream_t s);
+int simt_blocks_per_sm();
+int tc_blocks_per_sm();
+size_t tc_smem_bytes();
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+}  // namespace sp2i

@@ -1,0 +1,551 @@
+// tc_kernel.cu -- split-precision SP2 chain on the 5th-generation tensor cores.
+//
+// The activation f(X) = X^2 of every layer (Eq. activ) is evaluated from the
+// dual 16-bit representation X = X^(0) + X^(1) as X^(0)X^(0) + X^(0)X^(1) +
+// X^(1)X^(0) (the paper's A + B + B^T; the X^(1)X^(1) term is dropped), all
+// three products accumulated in one FP32 accumulator in tensor memory:
+//   S[i,j] = sum over one K-loop of length 3*np of A[i,k] * B[j,k],
+//   A = [op0 | op1 | op2], B = [op1 | op2 | op1]   (rows of X; X is symmetric),
+// with op0 = hi*2^11, op1 = hi, op2 = lo*2^11 for FP16 (every product carries
+// 2^11, removed in the epilogue) and op0 = op1 = hi, op2 = lo for BF16.
+//
+// Centred operands and accumulator-bias removal: the FP32 accumulator of the
+// tensor cores truncates once per MMA instruction, a relative bias of order
+// (K/16) 2^-24 that would make the chain converge to (1 + beta) times the
+// projector.  The operands are therefore the split of Y = X - I/2 (near
+// convergence Y^2 ~ I/4, so the product error is mostly a multiple of the
+// identity), the square is rebuilt as X^2 = Y^2 + X - I/4, and the identity
+// component of the error is measured exactly from Tr(Y^2) = ||Y||_F^2 (both
+// reduced in FP64) and carried to the next layer as a scalar offset c
+// (true X = stored X + c I).
+//
+// Kernel structure (one cooperative persistent launch for the whole chain):
+//   warp 0      TMA producer: 2-D tiled bulk copies (128B swizzle) of a 128 x 64
+//               A block and a 256 x 64 B block per stage into a 4-stage ring.
+//   warp 1      tcgen05.mma issuer (one thread): M=128, N=256, K=16 per
+//               instruction, FP32 accumulator in TMEM, double-buffered (2 x 256
+//               columns) so the epilogue of tile t overlaps the MMAs of t+1.
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, X_{n+1} = S or
+//               2 X_n - S, FP32 master + split operands written for the tile and
+//               its mirror (only tiles with rows <= columns are computed),
+//               compensated FP64 partials of Tr X and ||X||_F^2.
+// Between layers: grid barrier, then every CTA takes the same layer decision.
+// The response / adjoint stream reuses the same machinery with six K segments:
+// (C + C^T)[i,j] = sum_k X[i,k] Y[j,k] + Y[i,k] X[j,k] for symmetric X and Y.
+#include "device_common.cuh"
+
+namespace sp2i {
+
+namespace {
+
+constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;           // 16 KB
+constexpr uint32_t B_BYTES = TC_BN * TC_BK * 2;           // 32 KB
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;       // 48 KB
+constexpr uint32_t EPI_T_FLOATS = 32 * 33;                // transpose buffer per epilogue warp
+constexpr uint32_t TMEM_COLS = 512;                       // two 128 x 256 FP32 accumulators
+constexpr int EPI_WARPS = 4;
+
+struct TcSmemTail {
+    uint64_t full[TC_STAGES];
+    uint64_t empty[TC_STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint32_t tmem_base;
+    uint32_t pad;
+    double red[EPI_WARPS][4];
+    RoundCtl rc;
+};
+
+constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)TC_STAGES * STAGE_BYTES +
+                              (size_t)EPI_WARPS * EPI_T_FLOATS * 4 + sizeof(TcSmemTail);
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false on timeout or when the CTA is aborting.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const volatile int *abort,
+                                          unsigned long long timeout_ns, int *err) {
+#pragma unroll 1
+    for (int i = 0; i < 256; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (global_ns() - t0 > timeout_ns) {
+            set_error(err, SP2_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand in the 128-byte swizzle layout written by TMA: rows of 128 B,
+// 8-row atoms 1024 B apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A and B of one 16-bit
+// type (0 = FP16, 1 = BF16), both K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab) {
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Work description of one tile, identical for the three roles.
+// ---------------------------------------------------------------------------
+struct TileWork {
+    int inst, job, tile, bi, bj;
+    int resp;            // 0: square of X (3 segments), 1: C + C^T of X and Y (6 segments)
+    int xslot;           // X operand slot
+    int ybuf;            // Y input buffer (resp)
+    int flip;            // layer choice is 2X - X^2
+    int n;               // forward layer index of the input (square jobs)
+    float cf;            // offset c of the input X: true X = stored X + c I
+};
+
+__device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams &p, int g) {
+    TileWork w;
+    map_tile(rc, p.B, p.inst, g, w.inst, w.job, w.tile);
+    const InstDesc &d = p.inst[w.inst];
+    const int2 bt = p.tiles[d.tile_off + w.tile];
+    w.bi = bt.x;
+    w.bj = bt.y;
+    if (rc.phase == 1) {  // adjoint reverse: G_m from G_{m+1} and X_m
+        const int k = rc.layer[0];
+        const int m = rc.rev_total - 1 - k;
+        w.resp = 1;
+        w.xslot = m % d.nslots_x;
+        w.ybuf = k & 1;
+        w.flip = rc.chist[m + 1] == SP2_CHOICE_FLIP;
+        w.n = m;
+        w.cf = (float)rc.chist_c[m];
+    } else {
+        const int n = rc.layer[w.inst];
+        w.resp = w.job;
+        w.xslot = n % d.nslots_x;
+        w.ybuf = n & 1;
+        w.flip = rc.choice[w.inst] == SP2_CHOICE_FLIP;
+        w.n = n;
+        w.cf = (float)rc.coff[w.inst];
+    }
+    return w;
+}
+
+// Tensor maps of the K segment visited at position `pos`: returns the A and B maps.
+// The tensor cores' FP32 accumulator truncates once per MMA instruction, by up to
+// one unit in the last place of its current value.  The small cross-term segments
+// (hi x lo, lo x hi, 2^-11 of the result) are therefore accumulated first, while
+// the accumulator is still small, and the dominant hi x hi segment last.
+__device__ __forceinline__ void segment_maps(const InstDesc &d, const TileWork &w, int pos, const CUtensorMap *&am,
+                                             const CUtensorMap *&bm) {
+    const int s = w.resp ? (int)((0x305421u >> (4 * pos)) & 0xFu)   // segments 1, 2, 4, 5, then 0, 3
+                         : (int)((0x021u >> (4 * pos)) & 0xFu);     // segments 1, 2, then 0
+    const CUtensorMap *X3 = d.xmap + w.xslot * 3;
+    if (!w.resp) {
+        am = X3 + s;                           // op0, op1, op2
+        bm = X3 + (s == 1 ? 2 : 1);            // op1, op2, op1
+    } else {
+        const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
+        if (s < 3) {
+            am = X3 + s;                       // X op0, op1, op2
+            bm = Y3 + (s == 1 ? 2 : 1);        // Y op1, op2, op1
+        } else {
+            am = Y3 + (s == 4 ? 2 : 1);        // Y op1, op2, op1
+            bm = X3 + (s - 3);                 // X op0, op1, op2
+        }
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_constant__ RunParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stages = smem;
+    float *epi_T = (float *)(smem + (size_t)TC_STAGES * STAGE_BYTES);
+    TcSmemTail &tl = *(TcSmemTail *)(epi_T + EPI_WARPS * EPI_T_FLOATS);
+    RoundCtl &rc = tl.rc;
+    const volatile int *abort = &rc.abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&tl.full[s], 1);
+            mbar_init(&tl.empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tl.tfull[a], 1);
+            mbar_init(&tl.tempty[a], EPI_WARPS * 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        round_ctl_init(rc, p);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tl.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tl.tmem_base;
+
+    // Pipeline state, private to each role and carried across tiles and rounds.
+    uint32_t stage = 0, phase = 0;      // producer / MMA ring
+    uint32_t acc = 0, acc_phase = 0;    // MMA / epilogue accumulators
+    int pend[TC_STAGES];                // producer: parity + 1 of a load not yet released
+    for (int s = 0; s < TC_STAGES; ++s) pend[s] = 0;
+    const uint32_t idesc = idesc_f16(PREC == SP2_BF16_SPLIT ? 1u : 0u);
+    const float unscale = split_unscale<PREC>();
+
+    unsigned int target = 0;
+    bool first = true;
+    while (true) {
+        if (!first) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const bool withhold = (p.test_hook == 1 && blockIdx.x == 0 && target == 0);
+                target += gridDim.x;
+                if (!grid_barrier(p.barrier, target, p.err, p.timeout_ns, withhold)) rc.abort = 1;
+            }
+            __syncthreads();
+            if (rc.abort) break;
+        }
+        first = false;
+        if (threadIdx.x == 0) {
+            decide_round(rc, p);
+            // Make the previous round's global writes (other CTAs' epilogues,
+            // generic proxy) visible to this CTA's TMA reads (async proxy).
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        __syncthreads();
+        if (rc.abort || rc.total == 0) break;
+
+        if (warp == 0) {
+            // ------------------------- TMA producer -------------------------
+            if (lane == 0) {
+                for (int g = blockIdx.x; g < rc.total && !*abort; g += gridDim.x) {
+                    const TileWork w = describe(rc, p, g);
+                    const InstDesc &d = p.inst[w.inst];
+                    const int nkb = d.np / TC_BK;
+                    const int nseg = w.resp ? 6 : 3;
+                    for (int kb = 0; kb < nseg * nkb; ++kb) {
+                        const int s = kb / nkb;
+                        const int kx = (kb - s * nkb) * TC_BK;
+                        const CUtensorMap *am, *bm;
+                        segment_maps(d, w, s, am, bm);
+                        if (!mbar_wait(&tl.empty[stage], phase ^ 1u, abort, p.timeout_ns, p.err)) {
+                            rc.abort = 1;
+                            break;
+                        }
+                        pend[stage] = 0;
+                        uint8_t *sa = stages + (size_t)stage * STAGE_BYTES;
+                        mbar_expect_tx(&tl.full[stage], STAGE_BYTES);
+                        tma_load_2d(sa, am, kx, w.bi * TC_BM, &tl.full[stage]);
+                        tma_load_2d(sa + A_BYTES, bm, kx, w.bj * TC_BN, &tl.full[stage]);
+                        tma_load_2d(sa + A_BYTES + B_BYTES / 2, bm, kx, w.bj * TC_BN + TC_BN / 2, &tl.full[stage]);
+                        pend[stage] = (int)phase + 1;
+                        if (++stage == TC_STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+        } else if (warp == 1) {
+            // -------------------------- MMA issuer --------------------------
+            if (lane == 0) {
+                for (int g = blockIdx.x; g < rc.total && !*abort; g += gridDim.x) {
+                    const TileWork w = describe(rc, p, g);
+                    const InstDesc &d = p.inst[w.inst];
+                    const int nkb = (d.np / TC_BK) * (w.resp ? 6 : 3);
+                    if (!mbar_wait(&tl.tempty[acc], acc_phase ^ 1u, abort, p.timeout_ns, p.err)) {
+                        rc.abort = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + acc * TC_BN;
+                    bool ok = true;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                            rc.abort = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(stages + (size_t)stage * STAGE_BYTES);
+                        const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k) {
+                            umma_f16(d_tmem, sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
+                                     (kb | k) != 0 ? 1u : 0u);
+                        }
+                        umma_commit(&tl.empty[stage]);
+                        if (++stage == TC_STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    umma_commit(&tl.tfull[acc]);
+                    if (++acc == 2) {
+                        acc = 0;
+                        acc_phase ^= 1u;
+                    }
+                    if (!ok) break;
+                }
+            }
+        } else {
+            // --------------------------- epilogue ---------------------------
+            const int ew = warp - 2;
+            const int quarter = warp & 3;             // TMEM lanes this warp may access
+            float *T = epi_T + ew * EPI_T_FLOATS;
+            for (int g = blockIdx.x; g < rc.total; g += gridDim.x) {
+                const TileWork w = describe(rc, p, g);
+                const InstDesc &d = p.inst[w.inst];
+                const int np = d.np;
+                const size_t mat = (size_t)np * np;
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait(&tl.tfull[acc], acc_phase, abort, p.timeout_ns, p.err) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                tc_fence_after();
+                const float *old;
+                float *outf;
+                uint16_t *o0, *o1, *o2;
+                bool write0;
+                if (!w.resp) {
+                    old = d.xf[w.n & 1];
+                    outf = d.xf[(w.n + 1) & 1];
+                    uint16_t *base = d.xop + (size_t)((w.n + 1) % d.nslots_x) * 3 * mat;
+                    o0 = base;
+                    o1 = base + mat;
+                    o2 = base + 2 * mat;
+                    write0 = (PREC == SP2_FP16_SPLIT);
+                } else {
+                    const int yout = w.ybuf ^ 1;
+                    old = d.yf[w.ybuf];
+                    outf = d.yf[yout];
+                    uint16_t *base = d.yop + (size_t)yout * 3 * mat;
+                    o0 = base;
+                    o1 = base + mat;
+                    o2 = base + 2 * mat;
+                    write0 = false;
+                }
+                const int rw0 = w.bi * TC_BM + quarter * 32;  // first row of this warp
+                const int r = rw0 + lane;
+                const int nreal = d.n;
+                const float cf = w.cf;
+                FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f}, fp = {0.f, 0.f};
+                if (ok) {
+#pragma unroll 1
+                    for (int j = 0; j < TC_BN / 32; ++j) {
+                        const int cb = w.bj * TC_BN + j * 32;
+                        if (cb >= np) break;
+                        if (cb + 31 < rw0) continue;  // chunk entirely below the diagonal
+                        float v[32];
+                        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + j * 32, v);
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const int c = cb + jj;
+                            const float P = v[jj] * unscale;            // raw product
+                            const float xo = old[(size_t)c * np + r];   // (r, c) by symmetry, coalesced
+                            const bool dg = (r == c) && (r < nreal);
+                            float x;
+                            if (!w.resp) {
+                                // P = Y^2 for the stored operands Y = X - I/2; the true input is
+                                // X + cI, so X^2 = P + 2cY + cI + X - I/4 (c^2 is below FP32 here).
+                                const float yo = dg ? xo - 0.5f : xo;
+                                const float b = dg ? P - 0.25f : P;
+                                if (!w.flip) x = (b + fmaf(2.0f * cf, yo, dg ? cf : 0.0f)) + xo;  // X^2
+                                else x = xo - (b + fmaf(2.0f * cf, yo, dg ? -cf : 0.0f));        // 2X - X^2
+                            } else {
+                                // P = Y X1 + X1 Y; with X = Y + (1/2 + c) I the chain needs
+                                // X X1 + X1 X = P + (1 + 2c) X1.
+                                x = w.flip ? fmaf(1.0f - 2.0f * cf, xo, -P) : fmaf(1.0f + 2.0f * cf, xo, P);
+                            }
+                            if (r <= c) {
+                                const float y = (dg && !w.resp) ? x - 0.5f : x;  // next operands
+                                if (!w.resp) {
+                                    const float wgt = (r == c) ? 1.0f : 2.0f;
+                                    if (r == c) ff_add(ft, x);
+                                    ff_add_sq(fq, x, wgt);
+                                    ff_add_sq(fw, y, wgt);
+                                    if (dg) ff_add(fp, P);
+                                }
+                                if (r < c) {  // mirror (c, r): consecutive r across the warp
+                                    const size_t m = (size_t)c * np + r;
+                                    outf[m] = x;
+                                    uint16_t a0, a1, a2;
+                                    split3<PREC>(y, a0, a1, a2);
+                                    if (write0) o0[m] = a0;
+                                    o1[m] = a1;
+                                    o2[m] = a2;
+                                }
+                            }
+                            T[lane * 33 + jj] = x;
+                        }
+                        __syncwarp();
+                        // direct (r, c) stores through the transpose buffer
+#pragma unroll 4
+                        for (int ii = 0; ii < 32; ++ii) {
+                            const int rr = rw0 + ii, cc = cb + lane;
+                            if (rr <= cc) {
+                                const float x = T[ii * 33 + lane];
+                                const float y = (rr == cc && rr < nreal && !w.resp) ? x - 0.5f : x;
+                                const size_t m = (size_t)rr * np + cc;
+                                outf[m] = x;
+                                uint16_t a0, a1, a2;
+                                split3<PREC>(y, a0, a1, a2);
+                                if (write0) o0[m] = a0;
+                                o1[m] = a1;
+                                o2[m] = a2;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&tl.tempty[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1u;
+                }
+                if (!w.resp) {
+                    double red4[4] = {ff_value(ft), ff_value(fq), ff_value(fw), ff_value(fp)};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        for (int o = 16; o > 0; o >>= 1) red4[k] += __shfl_down_sync(0xffffffffu, red4[k], o);
+                    if (lane == 0)
+                        for (int k = 0; k < 4; ++k) tl.red[ew][k] = red4[k];
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (ew == 0 && lane == 0) {
+                        Part s4;
+                        s4.t = s4.q = s4.w = s4.p = 0.0;
+                        for (int k = 0; k < EPI_WARPS; ++k) {
+                            s4.t += tl.red[k][0];
+                            s4.q += tl.red[k][1];
+                            s4.w += tl.red[k][2];
+                            s4.p += tl.red[k][3];
+                        }
+                        d.part[(w.n + 1) & 1][w.tile] = s4;
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                }
+            }
+            // Order this round's generic-proxy stores before the async-proxy
+            // (TMA) reads of the next round, on any SM.
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __threadfence();
+        }
+    }
+
+    // ------------------------------ teardown ------------------------------
+    if (warp == 0 && lane == 0 && rc.abort) {
+        // Let loads still in flight land before the CTA exits (bounded wait).
+        for (int s = 0; s < TC_STAGES; ++s) {
+            if (pend[s]) {
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try_wait(&tl.full[s], (uint32_t)(pend[s] - 1)) && global_ns() - t0 < 50000000ull) {
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t tc_smem_bytes() { return SMEM_BYTES; }
+
+int tc_blocks_per_sm() {
+    int b = 0;
+    if (cudaFuncSetAttribute(k_tc_persistent<SP2_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES) != cudaSuccess)
+        return 0;
+    if (cudaFuncSetAttribute(k_tc_persistent<SP2_BF16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tc_persistent<SP2_FP16_SPLIT>, TC_THREADS, SMEM_BYTES) !=
+        cudaSuccess)
+        return 0;
+    return b;
+}
+
+cudaError_t launch_tc_persistent(const RunParams &p, int grid, cudaStream_t s) {
+    void *args[] = {(void *)&p};
+    const void *fn = (p.precision == SP2_BF16_SPLIT) ? (const void *)k_tc_persistent<SP2_BF16_SPLIT>
+                                                     : (const void *)k_tc_persistent<SP2_FP16_SPLIT>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(TC_THREADS), args, SMEM_BYTES, s);
+}
+
+}  // namespace sp2i

@@ -1,0 +1,330 @@
+"""Python binding of libsp2 (the C ABI in include/sp2.h), argument marshalling only.
+
+Every step of the SP2 chain runs in the library's CUDA kernels; this module only
+passes tensor pointers, the current CUDA stream and option structs through
+ctypes, and turns the returned statistics into Python objects.  There is no
+fallback: if ``libsp2.so`` has not been built, importing the functions below
+raises.
+
+Tensors may live on the GPU or on the host (the library stages host matrices
+through device memory).  H, H1 and G are float64; D, D1 and dH come back as
+float32, on the device of H.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsp2.so")
+
+OK, ERR_ARG, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED = range(8)
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
+STOP_NONE, STOP_TOL, STOP_STALL, STOP_MAX, STOP_TRIVIAL = range(5)
+CHOICE_INPUT, CHOICE_SQUARE, CHOICE_FLIP = -1, 0, 1
+MAX_LAYERS_LIMIT = 200
+
+
+class LayerStat(ctypes.Structure):
+    _fields_ = [("trace", ctypes.c_double), ("trace_sq", ctypes.c_double), ("idem", ctypes.c_double),
+                ("choice", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("layers", ctypes.c_int), ("stop_reason", ctypes.c_int), ("eps_min", ctypes.c_double),
+                ("eps_max", ctypes.c_double), ("band_energy", ctypes.c_double), ("trace_D", ctypes.c_double),
+                ("layer", ctypes.POINTER(LayerStat)), ("layer_cap", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("phase_ms", ctypes.c_float * 4)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_layers", ctypes.c_int), ("timeout_ms", ctypes.c_double),
+                ("user_bounds", ctypes.c_int), ("test_hook", ctypes.c_int), ("eps_min", ctypes.c_double),
+                ("eps_max", ctypes.c_double), ("profile", ctypes.c_int), ("reserved2", ctypes.c_int)]
+
+
+EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
+           "sp2_response", "sp2_response_workspace_bytes", "sp2_adjoint", "sp2_adjoint_workspace_bytes",
+           "sp2_density_batched", "sp2_density_batched_workspace_bytes", "sp2_apply_layers"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load libsp2.so (built by ``python -m paper_2107_02737_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with `python -m paper_2107_02737_gb300.build` "
+                           "(the SP2 path has no CPU fallback)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    c_d, c_i, c_sz, c_p = ctypes.c_double, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
+    P = ctypes.POINTER
+    lib.sp2_default_opts.argtypes = [P(Opts)]
+    lib.sp2_default_opts.restype = None
+    lib.sp2_status_string.argtypes = [c_i]
+    lib.sp2_status_string.restype = ctypes.c_char_p
+    lib.sp2_device_info.argtypes = [P(c_i), P(c_i), P(c_i)]
+    lib.sp2_device_info.restype = c_i
+    lib.sp2_density.argtypes = [c_p, c_i, c_d, c_d, c_p, P(Stats), P(Opts), c_p, c_sz, c_p]
+    lib.sp2_density.restype = c_i
+    lib.sp2_density_workspace_bytes.argtypes = [c_i, P(Opts)]
+    lib.sp2_density_workspace_bytes.restype = c_sz
+    lib.sp2_response.argtypes = [c_p, c_p, c_i, c_d, c_d, P(Stats), c_p, c_p, P(Stats), P(Opts), c_p, c_sz, c_p]
+    lib.sp2_response.restype = c_i
+    lib.sp2_response_workspace_bytes.argtypes = [c_i, P(Opts)]
+    lib.sp2_response_workspace_bytes.restype = c_sz
+    lib.sp2_adjoint.argtypes = [c_p, c_p, c_i, c_d, c_d, P(Stats), c_p, c_p, P(Stats), P(Opts), c_p, c_sz, c_p]
+    lib.sp2_adjoint.restype = c_i
+    lib.sp2_adjoint_workspace_bytes.argtypes = [c_i, c_i, P(Opts)]
+    lib.sp2_adjoint_workspace_bytes.restype = c_sz
+    lib.sp2_density_batched.argtypes = [c_i, P(c_p), P(c_i), P(c_d), c_d, P(c_p), P(Stats), P(Opts), c_p, c_sz, c_p]
+    lib.sp2_density_batched.restype = c_i
+    lib.sp2_density_batched_workspace_bytes.argtypes = [c_i, P(c_i), P(Opts)]
+    lib.sp2_density_batched_workspace_bytes.restype = c_sz
+    lib.sp2_apply_layers.argtypes = [c_p, c_i, P(c_i), c_i, c_p, P(Stats), P(Opts), c_p]
+    lib.sp2_apply_layers.restype = c_i
+    _lib = lib
+    return lib
+
+
+class SP2Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {load().sp2_status_string(status).decode()} (status {status})")
+
+
+@dataclasses.dataclass
+class Result:
+    status: int
+    layers: int
+    stop_reason: int
+    eps_min: float
+    eps_max: float
+    band_energy: float
+    trace_D: float
+    trace: List[float]
+    trace_sq: List[float]
+    idem: List[float]
+    choices: List[int]          # choice that produced X_n, n = 1..layers
+    raw: Stats = dataclasses.field(repr=False, default=None)
+    phase_ms: List[float] = dataclasses.field(default_factory=list)
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+
+def make_opts(precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0,
+              bounds: Optional[Sequence[float]] = None, profile: bool = False) -> Opts:
+    o = Opts()
+    load().sp2_default_opts(ctypes.byref(o))
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    o.precision = PRECISIONS[precision]
+    o.max_layers = int(max_layers)
+    o.timeout_ms = float(timeout_ms)
+    if bounds is not None:
+        o.user_bounds = 1
+        o.eps_min, o.eps_max = float(bounds[0]), float(bounds[1])
+    o.profile = 1 if profile else 0
+    return o
+
+
+def _new_stats(cap: int = MAX_LAYERS_LIMIT + 1):
+    arr = (LayerStat * cap)()
+    st = Stats()
+    st.layer = ctypes.cast(arr, ctypes.POINTER(LayerStat))
+    st.layer_cap = cap
+    st._keep = arr  # keep the array alive with the struct
+    return st
+
+
+def _result(status: int, st: Stats) -> Result:
+    n = min(st.layers + 1, st.layer_cap)
+    lay = [st.layer[k] for k in range(n)]
+    return Result(status, st.layers, st.stop_reason, st.eps_min, st.eps_max, st.band_energy, st.trace_D,
+                  [l.trace for l in lay], [l.trace_sq for l in lay], [l.idem for l in lay],
+                  [l.choice for l in lay[1:]], st, list(st.phase_ms))
+
+
+def _check(status: int, where: str):
+    if status not in (OK, ERR_NOT_CONVERGED):
+        raise SP2Error(status, where)
+
+
+def _stream_handle(t: torch.Tensor, stream) -> int:
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    dev = t.device if t.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    return int(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _square(t: torch.Tensor, name: str) -> int:
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError(f"{name} must be a square matrix")
+    return int(t.shape[0])
+
+
+def _f64(t: torch.Tensor, name: str) -> torch.Tensor:
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    return t.contiguous()
+
+
+def _ws_args(workspace: Optional[torch.Tensor]):
+    if workspace is None:
+        return None, 0
+    return ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+
+
+def workspace_bytes(n: int, kind: str = "density", precision: str = "fp16", layers: int = 0) -> int:
+    o = make_opts(precision)
+    lib = load()
+    if kind == "density":
+        return int(lib.sp2_density_workspace_bytes(n, ctypes.byref(o)))
+    if kind == "response":
+        return int(lib.sp2_response_workspace_bytes(n, ctypes.byref(o)))
+    if kind == "adjoint":
+        return int(lib.sp2_adjoint_workspace_bytes(n, layers, ctypes.byref(o)))
+    raise ValueError(kind)
+
+
+def density(H: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16", max_layers: int = 100,
+            timeout_ms: float = 2000.0, bounds=None, out: Optional[torch.Tensor] = None,
+            workspace: Optional[torch.Tensor] = None, stream=None, profile: bool = False):
+    """D = theta(mu I - H) by the DNN-SP2 chain; returns (D, Result)."""
+    H = _f64(H, "H")
+    n = _square(H, "H")
+    D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=H.device)
+    st = _new_stats()
+    o = make_opts(precision, max_layers, timeout_ms, bounds, profile)
+    ws, wsb = _ws_args(workspace)
+    s = load().sp2_density(ctypes.c_void_p(H.data_ptr()), n, float(n_occ), float(tol), ctypes.c_void_p(D.data_ptr()),
+                           ctypes.byref(st), ctypes.byref(o), ws, wsb, ctypes.c_void_p(_stream_handle(H, stream)))
+    _check(s, "sp2_density")
+    return D, _result(s, st)
+
+
+def response(H: torch.Tensor, H1: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16",
+             max_layers: int = 100, timeout_ms: float = 2000.0, fwd: Optional[Result] = None,
+             workspace: Optional[torch.Tensor] = None, stream=None):
+    """First-order response of the chain; returns (D, D1, Result)."""
+    H, H1 = _f64(H, "H"), _f64(H1, "H1")
+    n = _square(H, "H")
+    D = torch.empty((n, n), dtype=torch.float32, device=H.device)
+    D1 = torch.empty((n, n), dtype=torch.float32, device=H.device)
+    st = _new_stats()
+    o = make_opts(precision, max_layers, timeout_ms)
+    ws, wsb = _ws_args(workspace)
+    fp = ctypes.byref(fwd.raw) if fwd is not None else None
+    s = load().sp2_response(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(H1.data_ptr()), n, float(n_occ),
+                            float(tol), fp, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(D1.data_ptr()),
+                            ctypes.byref(st), ctypes.byref(o), ws, wsb, ctypes.c_void_p(_stream_handle(H, stream)))
+    _check(s, "sp2_response")
+    return D, D1, _result(s, st)
+
+
+def adjoint(H: torch.Tensor, G: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16",
+            max_layers: int = 100, timeout_ms: float = 2000.0, fwd: Optional[Result] = None,
+            workspace: Optional[torch.Tensor] = None, stream=None):
+    """Gradient dTr[D G]/dH of the chain by reverse accumulation; returns (D, dH, Result)."""
+    H, G = _f64(H, "H"), _f64(G, "G")
+    n = _square(H, "H")
+    D = torch.empty((n, n), dtype=torch.float32, device=H.device)
+    dH = torch.empty((n, n), dtype=torch.float32, device=H.device)
+    st = _new_stats()
+    o = make_opts(precision, max_layers, timeout_ms)
+    ws, wsb = _ws_args(workspace)
+    fp = ctypes.byref(fwd.raw) if fwd is not None else None
+    s = load().sp2_adjoint(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(G.data_ptr()), n, float(n_occ),
+                           float(tol), fp, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(dH.data_ptr()),
+                           ctypes.byref(st), ctypes.byref(o), ws, wsb, ctypes.c_void_p(_stream_handle(H, stream)))
+    _check(s, "sp2_adjoint")
+    return D, dH, _result(s, st)
+
+
+def density_batched(Hs: Sequence[torch.Tensor], n_occs: Sequence[int], tol: float = 1e-6,
+                    precision: str = "bf16", max_layers: int = 100, timeout_ms: float = 2000.0,
+                    outs: Optional[Sequence[torch.Tensor]] = None, workspace: Optional[torch.Tensor] = None,
+                    stream=None):
+    """Independent chains in one grouped launch; returns (list of D, list of Result, worst status)."""
+    B = len(Hs)
+    Hs = [_f64(h, f"H[{i}]") for i, h in enumerate(Hs)]
+    ns = [_square(h, f"H[{i}]") for i, h in enumerate(Hs)]
+    Ds = list(outs) if outs is not None else [torch.empty((n, n), dtype=torch.float32, device=h.device)
+                                                for n, h in zip(ns, Hs)]
+    sts = (Stats * B)()
+    keep = []
+    for b in range(B):
+        arr = (LayerStat * (MAX_LAYERS_LIMIT + 1))()
+        keep.append(arr)
+        sts[b].layer = ctypes.cast(arr, ctypes.POINTER(LayerStat))
+        sts[b].layer_cap = MAX_LAYERS_LIMIT + 1
+    hp = (ctypes.c_void_p * B)(*[h.data_ptr() for h in Hs])
+    dp = (ctypes.c_void_p * B)(*[d.data_ptr() for d in Ds])
+    nn = (ctypes.c_int * B)(*ns)
+    occ = (ctypes.c_double * B)(*[float(x) for x in n_occs])
+    o = make_opts(precision, max_layers, timeout_ms)
+    ws, wsb = _ws_args(workspace)
+    s = load().sp2_density_batched(B, hp, nn, occ, float(tol), dp, sts, ctypes.byref(o), ws, wsb,
+                                   ctypes.c_void_p(_stream_handle(Hs[0], stream)))
+    _check(s, "sp2_density_batched")
+    res = [_result(OK, sts[b]) for b in range(B)]
+    for r in res:
+        r.status = ERR_NOT_CONVERGED if r.stop_reason == STOP_MAX else OK
+        r._keep = keep  # the per-layer arrays behind r.raw
+    return Ds, res, s
+
+
+def apply_layers(X0: torch.Tensor, choices: Sequence[int], precision: str = "fp16", timeout_ms: float = 2000.0,
+                 stream=None):
+    """Apply the given layer signs to X0 (float32, symmetric); returns (X, Result)."""
+    if X0.dtype != torch.float32:
+        raise TypeError("X0 must be float32")
+    X0 = X0.contiguous()
+    n = _square(X0, "X0")
+    X = torch.empty_like(X0)
+    st = _new_stats()
+    o = make_opts(precision, MAX_LAYERS_LIMIT, timeout_ms)
+    ch = (ctypes.c_int * max(1, len(choices)))(*[int(c) for c in choices])
+    s = load().sp2_apply_layers(ctypes.c_void_p(X0.data_ptr()), n, ch, len(choices), ctypes.c_void_p(X.data_ptr()),
+                                ctypes.byref(st), ctypes.byref(o), ctypes.c_void_p(_stream_handle(X0, stream)))
+    _check(s, "sp2_apply_layers")
+    return X, _result(s, st)
+
+
+def device_info():
+    sm, ma, mi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    s = load().sp2_device_info(ctypes.byref(sm), ctypes.byref(ma), ctypes.byref(mi))
+    return s, sm.value, (ma.value, mi.value)
+
+
+class DensityMatrix(torch.autograd.Function):
+    """D(H) by the SP2 chain with a reverse-mode gradient through the chain.
+
+    backward(G) returns dTr[D G]/dH from ``sp2_adjoint`` replaying the forward's
+    layer signs and spectral bounds (both held constant).
+    """
+
+    @staticmethod
+    def forward(ctx, H, n_occ, tol=1e-6, precision="fp16", max_layers=100):
+        D, res = density(H, n_occ, tol=tol, precision=precision, max_layers=max_layers)
+        ctx.save_for_backward(H)
+        ctx.res, ctx.n_occ, ctx.tol, ctx.precision = res, n_occ, tol, precision
+        return D
+
+    @staticmethod
+    def backward(ctx, grad_D):
+        (H,) = ctx.saved_tensors
+        _, dH, _ = adjoint(H, grad_D.to(torch.float64).contiguous(), ctx.n_occ, tol=ctx.tol,
+                           precision=ctx.precision, fwd=ctx.res)
+        return dH.to(H.dtype), None, None, None, None

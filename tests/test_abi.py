@@ -1,0 +1,85 @@
+"""The C ABI on the CPU: the library loads without a GPU, exports every symbol that
+include/sp2.h declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2107_02737_gb300 import build
+import paper_2107_02737_gb300.sp2 as sp2
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return sp2.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sp2.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sp2_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"libsp2.so does not export {name}"
+    assert sorted(names) == sorted(sp2.EXPORTS)
+
+
+def test_default_opts_and_strings(lib):
+    o = sp2.make_opts()
+    assert (o.precision, o.max_layers, o.user_bounds, o.test_hook) == (1, 100, 0, 0)
+    assert o.timeout_ms == 2000.0
+    for code in range(8):
+        assert lib.sp2_status_string(code)
+    assert lib.sp2_status_string(0) == b"ok"
+
+
+def test_workspace_sizes_grow_with_n(lib):
+    a = sp2.workspace_bytes(256)
+    b = sp2.workspace_bytes(4096)
+    assert 0 < a < b
+    # FP16 split at N = 4096: two FP32 masters + two slots of three 16-bit operands.
+    assert b >= 2 * 4096 * 4096 * 4 + 2 * 3 * 4096 * 4096 * 2
+    assert sp2.workspace_bytes(512, "adjoint", layers=10) > sp2.workspace_bytes(512, "response")
+
+
+def _call_density(lib, n, n_occ, tol=1e-6, opts=None):
+    H = np.eye(max(n, 1))
+    D = np.zeros((max(n, 1), max(n, 1)), np.float32)
+    return lib.sp2_density(H.ctypes.data_as(ctypes.c_void_p), n, float(n_occ), tol,
+                           D.ctypes.data_as(ctypes.c_void_p), None, opts, None, 0, None)
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    assert _call_density(lib, 0, 0) == sp2.ERR_ARG
+    assert _call_density(lib, 8, 2.5) == sp2.ERR_ARG
+    assert _call_density(lib, 8, 9) == sp2.ERR_ARG
+    assert _call_density(lib, 8, -1) == sp2.ERR_ARG
+    assert _call_density(lib, 8, 4, tol=-1.0) == sp2.ERR_ARG
+    o = sp2.make_opts(max_layers=0)
+    assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
+    o = sp2.make_opts(bounds=(1.0, 0.0))
+    assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
+
+
+def test_apply_layers_rejects_bad_choices(lib):
+    X = np.zeros((4, 4), np.float32)
+    ch = (ctypes.c_int * 2)(0, 2)
+    r = lib.sp2_apply_layers(X.ctypes.data_as(ctypes.c_void_p), 4, ch, 2, X.ctypes.data_as(ctypes.c_void_p),
+                             None, None, None)
+    assert r == sp2.ERR_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(sp2, "_lib", None)
+    monkeypatch.setattr(sp2, "_LIB_PATH", str(tmp_path / "libsp2.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        sp2.load()

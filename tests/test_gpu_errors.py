@@ -1,0 +1,65 @@
+"""Error paths on the GPU: non-finite input, degenerate and gapless spectra, and a
+device wait that runs out (a barrier arrival that is withheld on purpose) --
+each returns a status and leaves the context usable."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import density as odens
+from paper_2107_02737_gb300 import inputs
+import paper_2107_02737_gb300.sp2 as sp2
+from tests._gpu import TOL_D, dev, fro_err, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp32"])
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_nonfinite_input(precision, bad):
+    H = inputs.gapped_random(64, 32, np.random.default_rng(2)).H
+    H[3, 7] = H[7, 3] = bad
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.density(dev(H), 32, precision=precision)
+    assert e.value.status == sp2.ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp32"])
+def test_scalar_hamiltonian_is_not_converged(precision):
+    D, res = sp2.density(dev(np.eye(40) * 0.3), 10, precision=precision)
+    assert res.status == sp2.ERR_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp32"])
+def test_gapless_spectrum_hits_layer_limit(precision):
+    H = np.diag([-1.0, 0.0, 0.0, 1.0])
+    D, res = sp2.density(dev(H), 2, precision=precision, max_layers=30)
+    assert res.status == sp2.ERR_NOT_CONVERGED and res.stop_reason == sp2.STOP_MAX
+    assert res.layers == 30
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp32"])
+def test_barrier_timeout_returns_status(precision):
+    ham = inputs.gapped_random(256, 128, np.random.default_rng(4))
+    o = sp2.make_opts(precision, timeout_ms=100.0)
+    o.test_hook = 1
+    D = torch.empty((256, 256), dtype=torch.float32, device="cuda")
+    st = sp2._new_stats()
+    H = dev(ham.H)
+    import ctypes
+    s = sp2.load().sp2_density(ctypes.c_void_p(H.data_ptr()), 256, 128.0, 1e-6, ctypes.c_void_p(D.data_ptr()),
+                               ctypes.byref(st), ctypes.byref(o), None, 0,
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert s == sp2.ERR_TIMEOUT
+    # the context is still usable
+    D2, res = sp2.density(H, 128, precision=precision)
+    assert fro_err(host(D2), odens.density_matrix(ham.H, 128)) <= TOL_D[precision]
+
+
+def test_unsupported_combinations():
+    H = dev(inputs.gapped_random(32, 16, np.random.default_rng(3)).H)
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.response(H, H, 16, precision="fp32")
+    assert e.value.status == sp2.ERR_UNSUPPORTED
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.density(H, 16.5)
+    assert e.value.status == sp2.ERR_ARG

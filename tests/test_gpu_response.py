@@ -1,0 +1,84 @@
+"""Parity of sp2_response (the forward-mode derivative of the chain) with the oracle:
+the FP64 chain response replaying the GPU's layer signs and bounds, the eigenbasis
+perturbation formula for theta(mu I - H), and central differences of the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import density as odens
+from oracle import sp2 as osp2
+from paper_2107_02737_gb300 import inputs
+import paper_2107_02737_gb300.sp2 as sp2
+from tests._gpu import TOL_D, dev, fro_err, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+# ||D1 - D1_ref||_F / ||D1_ref||_F for the split precisions (FP32 accumulation of a
+# chain whose derivative amplifies near-gap components by up to 1/gap).
+TOL_D1 = {"fp16": 2e-3, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module", params=[256, 300])
+def case(request):
+    n = request.param
+    ham = inputs.gapped_random(n, n // 2, inputs.rng_for(3, n))
+    rng = inputs.rng_for(3, 10 + n)
+    return ham, inputs.symmetric_gaussian(n, rng) * 0.01
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_response_matches_chain_and_theta(case, precision):
+    ham, H1 = case
+    D, D1, res = sp2.response(dev(ham.H), dev(H1), ham.n_occ, precision=precision)
+    assert res.converged
+    assert fro_err(host(D), odens.density_from_eigensystem(ham.eigvecs, ham.n_occ)) <= TOL_D[precision]
+    chain = osp2.chain_response(ham.H, H1, res.choices, res.eps_min, res.eps_max)
+    theta = odens.response_from_eigensystem(ham.eigvals, ham.eigvecs, H1, ham.n_occ)
+    g = host(D1)
+    print(f"\n{precision} N={ham.n}: rel err vs chain {rel_err(g, chain):.2e}, vs theta {rel_err(g, theta):.2e}")
+    assert rel_err(g, chain) <= TOL_D1[precision]
+    assert rel_err(g, theta) <= TOL_D1[precision] + 1e-3
+    assert np.array_equal(g, g.T)
+    assert abs(np.trace(g)) <= 1e-3 * np.linalg.norm(g)
+
+
+def test_response_matches_oracle_central_differences(case):
+    ham, H1 = case
+    h = 1e-4
+    fd = (odens.density_matrix(ham.H + h * H1, ham.n_occ) - odens.density_matrix(ham.H - h * H1, ham.n_occ)) / (2 * h)
+    _, D1, _ = sp2.response(dev(ham.H), dev(H1), ham.n_occ, precision="fp16")
+    assert rel_err(host(D1), fd) <= TOL_D1["fp16"] + 1e-3
+
+
+def test_response_replaying_forward_matches_density(case):
+    ham, H1 = case
+    D, res = sp2.density(dev(ham.H), ham.n_occ, precision="fp16")
+    D2, D1, r2 = sp2.response(dev(ham.H), dev(H1), ham.n_occ, precision="fp16", fwd=res)
+    assert r2.choices == res.choices
+    assert torch.equal(D, D2)
+    D3, D1b, r3 = sp2.response(dev(ham.H), dev(H1), ham.n_occ, precision="fp16")
+    assert torch.equal(D1, D1b)  # deciding on device reproduces the same chain
+
+
+def test_response_is_linear(case):
+    ham, H1 = case
+    _, a, _ = sp2.response(dev(ham.H), dev(H1), ham.n_occ, precision="fp16")
+    _, b, _ = sp2.response(dev(ham.H), dev(-4.0 * H1), ham.n_occ, precision="fp16")
+    # power-of-two scaling of the input stream is exact
+    assert torch.allclose(b, -4.0 * a, rtol=1e-6, atol=1e-7)
+
+
+def test_response_differentiation_workload_4096():
+    ham, H1, _ = inputs.differentiation_workload(4096)
+    D, D1, res = sp2.response(dev(ham.H), dev(H1), ham.n_occ, precision="fp16")
+    assert res.converged
+    # sampled rows of the eigenbasis formula: D1 = C (C^T H1 C o F) C^T
+    C, lam = ham.eigvecs, ham.eigvals
+    F = odens.response_weights(lam, ham.n_occ)
+    M = (C.T @ H1 @ C) * F
+    pick = np.random.default_rng(1).choice(ham.n, size=6, replace=False)
+    ref = C[pick] @ M @ C.T
+    got = host(D1[torch.tensor(pick, device="cuda")])
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"\nN=4096 response: layers={res.layers} sampled-row rel err {err:.2e}")
+    assert err <= 1e-2
