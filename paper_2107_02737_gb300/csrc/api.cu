@@ -153,13 +153,8 @@ int ntiles_for(int path, int np) {
     return (int)t.size();
 }
 
-int init_blocks_host(int np) {
-    size_t work = (size_t)np * np / 4, per = 256 * 8;
-    size_t g = (work + per - 1) / per;
-    if (g < 1) g = 1;
-    if (g > (size_t)INIT_BLOCKS_MAX) g = INIT_BLOCKS_MAX;
-    return (int)g;
-}
+// Must equal the device-side init_blocks_for: one partial per input-layer block.
+int init_blocks_host(int np) { return np < INIT_BLOCKS_MAX ? np : INIT_BLOCKS_MAX; }
 
 struct Plan {
     int mode, path, precision;

@@ -145,34 +145,34 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
     float *xf = d.xf[0];
     uint16_t *op0 = d.xop, *op1 = d.xop + (size_t)np * np, *op2 = d.xop + 2 * (size_t)np * np;
     FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
-    const size_t total4 = (size_t)np * np / 4;
-    for (size_t e4 = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; e4 < total4; e4 += (size_t)gridDim.x * AUX_THREADS) {
-        const size_t idx = e4 * 4;
-        const int i = (int)(idx / np), j0 = (int)(idx % np);
-        float x[4], y[4];
+    // Rows are strided over blocks, four consecutive columns per thread: no
+    // index divisions on the hot loop.
+    for (int i = blockIdx.x; i < np; i += gridDim.x) {
+        const double *hrow = d.H + (size_t)i * n;
+        for (int j0 = threadIdx.x * 4; j0 < np; j0 += AUX_THREADS * 4) {
+            const size_t idx = (size_t)i * np + j0;
+            float x[4], y[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + q;
-            float v = 0.0f;
-            if (i < n && j < n) {
-                const double h = d.H[(size_t)i * n + j];
-                v = (float)((((i == j) ? emax : 0.0) - h) * inv);
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + q;
+                float v = 0.0f;
+                if (i < n && j < n) v = (float)((((i == j) ? emax : 0.0) - hrow[j]) * inv);
+                x[q] = v;
+                y[q] = (i == j && i < n) ? v - 0.5f : v;
+                if (i == j) ff_add(ft, v);
+                ff_add_sq(fq, v, 1.0f);
+                if (PATH == PATH_TC) ff_add_sq(fw, y[q], 1.0f);
             }
-            x[q] = v;
-            y[q] = (i == j && i < n) ? v - 0.5f : v;
-            if (i == j) ff_add(ft, v);
-            ff_add_sq(fq, v, 1.0f);
-            if (PATH == PATH_TC) ff_add_sq(fw, y[q], 1.0f);
-        }
-        *(float4 *)(xf + idx) = make_float4(x[0], x[1], x[2], x[3]);
-        if (PATH == PATH_TC) {
-            // operands of the first square: the split of Y_0 = X_0 - I/2
-            uint16_t a[4], b[4], c[4];
+            *(float4 *)(xf + idx) = make_float4(x[0], x[1], x[2], x[3]);
+            if (PATH == PATH_TC) {
+                // operands of the first square: the split of Y_0 = X_0 - I/2
+                uint16_t a[4], b[4], c[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) split3<PREC>(y[q], a[q], b[q], c[q]);
-            if (PREC == SP2_FP16_SPLIT) *(ushort4 *)(op0 + idx) = make_ushort4(a[0], a[1], a[2], a[3]);
-            *(ushort4 *)(op1 + idx) = make_ushort4(b[0], b[1], b[2], b[3]);
-            *(ushort4 *)(op2 + idx) = make_ushort4(c[0], c[1], c[2], c[3]);
+                for (int q = 0; q < 4; ++q) split3<PREC>(y[q], a[q], b[q], c[q]);
+                if (PREC == SP2_FP16_SPLIT) *(ushort4 *)(op0 + idx) = make_ushort4(a[0], a[1], a[2], a[3]);
+                *(ushort4 *)(op1 + idx) = make_ushort4(b[0], b[1], b[2], b[3]);
+                *(ushort4 *)(op2 + idx) = make_ushort4(c[0], c[1], c[2], c[3]);
+            }
         }
     }
     double3 s = block_sum3(ff_value(ft), ff_value(fq), ff_value(fw));
@@ -201,21 +201,22 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x_from(InstDesc *inst, con
     float *xf = d.xf[0];
     uint16_t *op0 = d.xop, *op1 = d.xop + (size_t)np * np, *op2 = d.xop + 2 * (size_t)np * np;
     FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
-    const size_t total = (size_t)np * np;
-    for (size_t idx = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; idx < total; idx += (size_t)gridDim.x * AUX_THREADS) {
-        const int i = (int)(idx / np), j = (int)(idx % np);
-        const float v = (i < n && j < n) ? X0[(size_t)i * n + j] : 0.0f;
-        xf[idx] = v;
-        if (i == j) ff_add(ft, v);
-        ff_add_sq(fq, v, 1.0f);
-        if (PATH == PATH_TC) {
-            const float y = (i == j && i < n) ? v - 0.5f : v;
-            ff_add_sq(fw, y, 1.0f);
-            uint16_t a, b, c;
-            split3<PREC>(y, a, b, c);
-            if (PREC == SP2_FP16_SPLIT) op0[idx] = a;
-            op1[idx] = b;
-            op2[idx] = c;
+    for (int i = blockIdx.x; i < np; i += gridDim.x) {
+        for (int j = threadIdx.x; j < np; j += AUX_THREADS) {
+            const size_t idx = (size_t)i * np + j;
+            const float v = (i < n && j < n) ? X0[(size_t)i * n + j] : 0.0f;
+            xf[idx] = v;
+            if (i == j) ff_add(ft, v);
+            ff_add_sq(fq, v, 1.0f);
+            if (PATH == PATH_TC) {
+                const float y = (i == j && i < n) ? v - 0.5f : v;
+                ff_add_sq(fw, y, 1.0f);
+                uint16_t a, b, c;
+                split3<PREC>(y, a, b, c);
+                if (PREC == SP2_FP16_SPLIT) op0[idx] = a;
+                op1[idx] = b;
+                op2[idx] = c;
+            }
         }
     }
     double3 s = block_sum3(ff_value(ft), ff_value(fq), ff_value(fw));
@@ -246,9 +247,9 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode
     const double yscale = ldexp(1.0, -ex);
     const double c = coef * yscale;
     uint16_t *op1 = d.yop + (size_t)np * np, *op2 = d.yop + 2 * (size_t)np * np;
-    const size_t total = (size_t)np * np;
-    for (size_t idx = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; idx < total; idx += (size_t)gridDim.x * AUX_THREADS) {
-        const int i = (int)(idx / np), j = (int)(idx % np);
+    for (int i = blockIdx.x; i < np; i += gridDim.x)
+        for (int j = threadIdx.x; j < np; j += AUX_THREADS) {
+        const size_t idx = (size_t)i * np + j;
         double a = 0.0, b = 0.0;
         if (i < n && j < n) {
             a = d.H1[(size_t)i * n + j];
@@ -278,15 +279,16 @@ __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mo
     if (mode == MODE_RESPONSE) ys = (float)(1.0 / ctl->y_scale);
     if (mode == MODE_ADJOINT) ys = (float)(-1.0 / (ctl->y_scale * (ctl->eps_max - ctl->eps_min)));
     double e = 0.0, tr = 0.0;
-    const size_t total = (size_t)n * n;
-    for (size_t idx = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; idx < total; idx += (size_t)d.fin_blocks * AUX_THREADS) {
-        const int i = (int)(idx / n), j = (int)(idx % n);
-        float x = X[(size_t)i * np + j];
-        if (i == j) x += xoff;  // true X_L = stored X_L + c_L I
-        if (d.out) d.out[idx] = x;
-        if (d.H) e += (double)x * d.H[idx];
-        if (i == j) tr += x;
-        if (mode == MODE_RESPONSE || mode == MODE_ADJOINT) d.out1[idx] = Y[(size_t)i * np + j] * ys;
+    for (int i = blockIdx.x; i < n; i += d.fin_blocks) {
+        for (int j = threadIdx.x; j < n; j += AUX_THREADS) {
+            const size_t idx = (size_t)i * n + j;
+            float x = X[(size_t)i * np + j];
+            if (i == j) x += xoff;  // true X_L = stored X_L + c_L I
+            if (d.out) d.out[idx] = x;
+            if (d.H) e += (double)x * d.H[idx];
+            if (i == j) tr += x;
+            if (mode == MODE_RESPONSE || mode == MODE_ADJOINT) d.out1[idx] = Y[(size_t)i * np + j] * ys;
+        }
     }
     double2 s = block_sum2(e, tr);
     if (threadIdx.x == 0) d.fin_part[blockIdx.x] = s;
@@ -332,7 +334,8 @@ cudaError_t launch_maxabs(InstDesc *inst, int B, int max_n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int init_blocks_for(int np) { return grid_for((size_t)np * np / 4, AUX_THREADS * 8, INIT_BLOCKS_MAX); }
+// One or more rows per block; the host sizes the partial buffers with the same rule.
+int init_blocks_for(int np) { return np < INIT_BLOCKS_MAX ? np : INIT_BLOCKS_MAX; }
 
 cudaError_t launch_init_x(InstDesc *inst, int B, int max_np, int path, int precision, bool user_bounds,
                           cudaStream_t s) {

@@ -184,9 +184,48 @@ __device__ __forceinline__ void round_ctl_init(RoundCtl &rc, const RunParams &p)
     rc.chist[0] = SP2_CHOICE_INPUT;
 }
 
-// Thread 0 of every CTA: reduce the partials of the layer just finished,
-// record statistics (CTA 0), apply the stop rule and pick the next signs.
-__device__ inline void decide_round(RoundCtl &rc, const RunParams &p) {
+// All threads of a CTA: sum, for every instance still running, the per-tile
+// partials of the layer just finished into sums[4 i .. 4 i + 3] (shared memory).
+// Thread k adds entries k, k + blockDim.x, ... in increasing order, then a fixed
+// shuffle tree and a fixed sum over warps: the same code on every CTA gives the
+// same bits, so every CTA takes the same decision.
+__device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams &p, double *sums, double *wscratch) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (rc.phase == 1) return;
+    for (int i = 0; i < p.B; ++i) {
+        if (!rc.active[i]) continue;
+        const InstDesc &d = p.inst[i];
+        const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
+        const int cnt = (n == 0) ? d.ctl->init_parts : d.ntiles;
+        const Part *part = d.part[n & 1];
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+        for (int k = tid; k < cnt; k += blockDim.x) {
+            const Part v = part[k];
+            a[0] += v.t;
+            a[1] += v.q;
+            a[2] += v.w;
+            a[3] += v.p;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+        if (lane == 0)
+            for (int c = 0; c < 4; ++c) wscratch[wid * 4 + c] = a[c];
+        __syncthreads();
+        if (tid == 0) {
+            double r[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int w = 0; w < nw; ++w)
+                for (int c = 0; c < 4; ++c) r[c] += wscratch[w * 4 + c];
+            for (int c = 0; c < 4; ++c) sums[i * 4 + c] = r[c];
+        }
+        __syncthreads();
+    }
+}
+
+// Thread 0 of every CTA: take the sums of the layer just finished, record
+// statistics (CTA 0), apply the stop rule and pick the next signs.
+__device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const double *sums) {
     const bool writer = (blockIdx.x == 0);
     if (ld_volatile(p.err) != 0) {
         rc.abort = 1;
@@ -216,16 +255,7 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p) {
         if (rc.active[i]) {
             if (rc.ran[i]) rc.layer[i] += 1;
             const int n = rc.layer[i];
-            const int cnt = (n == 0) ? ctl->init_parts : d.ntiles;
-            const Part *part = d.part[n & 1];
-            double ts = 0.0, qs = 0.0, ws = 0.0, ps = 0.0;
-            for (int k = 0; k < cnt; ++k) {
-                const Part v = part[k];
-                ts += v.t;
-                qs += v.q;
-                ws += v.w;
-                ps += v.p;
-            }
+            const double ts = sums[i * 4 + 0], qs = sums[i * 4 + 1], ws = sums[i * 4 + 2], ps = sums[i * 4 + 3];
             const int made = (n == 0) ? SP2_CHOICE_INPUT : rc.choice[i];
             // Accumulator bias of the square that made X_n: in exact arithmetic
             // Tr(Y^2) = ||Y||_F^2 for the symmetric operand Y, so the deficit of the

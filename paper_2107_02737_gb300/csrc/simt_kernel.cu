@@ -134,7 +134,10 @@ __global__ void __launch_bounds__(SIMT_THREADS) k_simt_persistent(const __grid_c
             if (rc.abort) break;
         }
         first = false;
-        if (threadIdx.x == 0) decide_round(rc, p);
+        // The operand staging buffers are idle here: use them for the sums.
+        double *sums = (double *)&sm.A[0][0][0];
+        reduce_round_partials(rc, p, sums, sums + 4 * MAX_BATCH);
+        if (threadIdx.x == 0) decide_round(rc, p, sums);
         __syncthreads();
         if (rc.abort || rc.total == 0) break;
         for (int g = blockIdx.x; g < rc.total; g += gridDim.x) {

@@ -36,8 +36,8 @@ constexpr int SIMT_T = 128;         // FP32 SIMT tile (square)
 constexpr int SIMT_THREADS = 256;
 constexpr int MAX_BATCH = 128;
 constexpr int MAX_L = SP2_MAX_LAYERS_LIMIT;
-constexpr int INIT_BLOCKS_MAX = 512;
-constexpr int FIN_BLOCKS_MAX = 256;
+constexpr int INIT_BLOCKS_MAX = 1024;
+constexpr int FIN_BLOCKS_MAX = 1024;
 constexpr int LO_SHIFT = 11;        // FP16 lo parts are stored times 2^11 (exact scaling)
 constexpr double STALL_MAX = 1e-2;
 

@@ -278,8 +278,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             if (rc.abort) break;
         }
         first = false;
+        // The epilogue transpose buffers are idle here: use them for the sums.
+        reduce_round_partials(rc, p, (double *)epi_T, (double *)epi_T + 4 * MAX_BATCH);
         if (threadIdx.x == 0) {
-            decide_round(rc, p);
+            decide_round(rc, p, (const double *)epi_T);
             // Make the previous round's global writes (other CTAs' epilogues,
             // generic proxy) visible to this CTA's TMA reads (async proxy).
             asm volatile("fence.proxy.async.global;" ::: "memory");
