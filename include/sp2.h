@@ -210,6 +210,30 @@ sp2_status sp2_density_batched(int B, const double *const *H, const int *N, cons
 sp2_status sp2_apply_layers(const float *X0, int N, const int *choices, int n_layers, float *X,
                             sp2_stats *st, const sp2_opts *o, void *stream);
 
+/*
+ * sp2_density_noalloc -- sp2_density without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory once running, such as an MD engine whose memory
+ * is reserved by its own pool or by another framework's caching allocator (a
+ * new allocation can fail or fragment it), or a step loop that cannot afford
+ * an allocation's latency.  The workspace is a statically allocated device
+ * array of 6 MiB, present on every GPU that loads the library until the
+ * process exits, which holds one solve of N <= SP2_NOALLOC_MAX_N.
+ *   H, D   must be device pointers (staging host data would allocate);
+ *          arguments and results are those of sp2_density.
+ *   o      may be NULL; o->profile must be 0.
+ * Returns SP2_ERR_ARG for N > SP2_NOALLOC_MAX_N, host pointers or profiling.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Every call uses the same array: calls whose work overlaps on the GPU (on
+ * different streams, or from different host threads) race and corrupt each
+ * other's results, so serialise them.  Each call initialises the parts of the
+ * array that must start at zero, so no state carries over between calls.
+ */
+#define SP2_NOALLOC_MAX_N 512
+sp2_status sp2_density_noalloc(const double *H, int N, double n_occ, double tol, float *D,
+                               sp2_stats *st, const sp2_opts *o, void *stream);
+
 /* Number of streaming multiprocessors and whether the current device runs this
  * library's kernels (compute capability 10.3). */
 sp2_status sp2_device_info(int *sm_count, int *cc_major, int *cc_minor);

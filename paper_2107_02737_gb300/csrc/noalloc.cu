@@ -1,0 +1,69 @@
+// noalloc.cu -- sp2_density for callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc once they are running: an MD engine whose
+// device memory is already reserved by its own pool or by another framework's
+// caching allocator (a fresh allocation can fail or fragment that pool), or a
+// time-critical step loop that cannot afford an allocation's latency.  For them
+// this file keeps the whole workspace of one solve in a statically allocated
+// device array, sized for N <= SP2_NOALLOC_MAX_N, and runs the ordinary
+// sp2_density kernels on it.
+//
+// The array lives in every GPU that loads the library, for the life of the
+// process.  Host code may not use its name as a device address: the address is
+// obtained once per device with cudaGetSymbolAddress, with that device current.
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "sp2.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)6 << 20;  // 6 MiB: the workspace of one N <= 512 solve
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" sp2_status sp2_density_noalloc(const double *H, int N, double n_occ, double tol, float *D,
+                                          sp2_stats *st, const sp2_opts *o, void *stream) {
+    if (N < 1 || N > SP2_NOALLOC_MAX_N) return SP2_ERR_ARG;
+    if (!H || !D || !on_device(H) || !on_device(D)) return SP2_ERR_ARG;  // staging host data would allocate
+    if (o && o->profile) return SP2_ERR_ARG;                              // timing events are not allowed here
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SP2_ERR_CUDA;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_scratch_addr[dev]) {
+            // First call on this device: resolve the device address of the array
+            // (with this device current).
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return SP2_ERR_CUDA;
+            }
+            g_scratch_addr[dev] = p;
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    if (sp2_density_workspace_bytes(N, o) > kScratchBytes) return SP2_ERR_ARG;
+    // sp2_density clears every word of its workspace that must start at zero
+    // (barrier counter, error word, control blocks) and writes every partial
+    // and matrix before reading it, so stale contents of the shared array from
+    // an earlier call do not leak into this one.
+    return sp2_density(H, N, n_occ, tol, D, st, o, scratch, kScratchBytes, stream);
+}

@@ -48,7 +48,9 @@ class Opts(ctypes.Structure):
 
 EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
            "sp2_response", "sp2_response_workspace_bytes", "sp2_adjoint", "sp2_adjoint_workspace_bytes",
-           "sp2_density_batched", "sp2_density_batched_workspace_bytes", "sp2_apply_layers"]
+           "sp2_density_batched", "sp2_density_batched_workspace_bytes", "sp2_apply_layers",
+           "sp2_density_noalloc"]
+NOALLOC_MAX_N = 512
 
 _lib = None
 
@@ -92,6 +94,8 @@ def load() -> ctypes.CDLL:
     lib.sp2_density_batched_workspace_bytes.restype = c_sz
     lib.sp2_apply_layers.argtypes = [c_p, c_i, P(c_i), c_i, c_p, P(Stats), P(Opts), c_p]
     lib.sp2_apply_layers.restype = c_i
+    lib.sp2_density_noalloc.argtypes = [c_p, c_i, c_d, c_d, c_p, P(Stats), P(Opts), c_p]
+    lib.sp2_density_noalloc.restype = c_i
     _lib = lib
     return lib
 
@@ -300,6 +304,25 @@ def apply_layers(X0: torch.Tensor, choices: Sequence[int], precision: str = "fp1
                                 ctypes.byref(st), ctypes.byref(o), ctypes.c_void_p(_stream_handle(X0, stream)))
     _check(s, "sp2_apply_layers")
     return X, _result(s, st)
+
+
+def density_noalloc(H: torch.Tensor, n_occ: int, out: torch.Tensor, tol: float = 1e-6, precision: str = "fp16",
+                    max_layers: int = 100, timeout_ms: float = 2000.0, stream=None):
+    """sp2_density on the library's static device workspace (N <= 512, device tensors only).
+
+    For callers that must not allocate device memory while running: nothing is
+    allocated here either, so ``out`` (float32, N x N, on the device of H) is
+    required.  Calls that overlap on the GPU share the workspace and race.
+    """
+    H = _f64(H, "H")
+    n = _square(H, "H")
+    st = _new_stats()
+    o = make_opts(precision, max_layers, timeout_ms)
+    s = load().sp2_density_noalloc(ctypes.c_void_p(H.data_ptr()), n, float(n_occ), float(tol),
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.byref(st), ctypes.byref(o),
+                                   ctypes.c_void_p(_stream_handle(H, stream)))
+    _check(s, "sp2_density_noalloc")
+    return out, _result(s, st)
 
 
 def device_info():
