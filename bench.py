@@ -284,7 +284,7 @@ def main():
                    "n": n, "n_occ": n_occ, "precision": f"split {args.precision} hi/lo, FP32 accumulation",
                    "l2": "inputs larger than L2 (H is 537 MB FP64; split operands 402 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "layers": L, "stop_reason": res.stop_reason,
+        "layers": L, "stop_reason": res.stop_reason, "cta_group": res.cta_group,
         "accuracy": {"fro_err_vs_fp64_per_sqrtN": None, "idempotency_fro": idem, "trace_err": res.trace_D - n_occ,
                      "commutator_fro": comm, "band_energy": res.band_energy},
         "fp32_simt": {"ms_per_step": ms32, "value": eff_tflops(r32.layers, n, ms32), "unit": "TFLOP/s",

@@ -100,7 +100,7 @@ typedef struct {
     double trace_D;        /* Tr D in FP64 from the FP32 D */
     sp2_layer_stat *layer;
     int layer_cap;
-    int reserved;
+    int cta_group;         /* CTAs per tensor-core tile the call used (0 on the FP32 path) */
     float phase_ms[4];     /* with sp2_opts.profile: device time of [0] bounds + input layer
                               (+ response / adjoint stream start), [1] the persistent layer
                               kernel, [2] output copy and FP64 reductions, [3] all three;
@@ -118,7 +118,8 @@ typedef struct {
     double eps_min;
     double eps_max;
     int profile;          /* 1 = record per-phase device times into sp2_stats.phase_ms */
-    int reserved2;
+    int cta_group;        /* tensor-core tiles: 0 = choose (default), 1 = one CTA per 128 x 256
+                             tile, 2 = a CTA pair per 256 x 256 tile (M = 256 MMAs) */
 } sp2_opts;
 
 /* Fill `o` with the defaults. */

@@ -135,29 +135,43 @@ struct Carver {
 
 // Tile tables: SIMT uses square 128-tiles with bi <= bj; the tensor-core path
 // uses 128 x 256 tiles containing at least one element with row <= column.
-void build_tiles(int path, int np, std::vector<int2> &t) {
-    if (path == PATH_SIMT) {
-        const int nb = np / SIMT_T;
-        for (int bj = 0; bj < nb; ++bj)
-            for (int bi = 0; bi <= bj; ++bi) t.push_back(make_int2(bi, bj));
-    } else {
-        const int nbi = np / TC_BM, nbj = (np + TC_BN - 1) / TC_BN;
-        for (int bj = 0; bj < nbj; ++bj)
-            for (int bi = 0; bi < nbi && bi * TC_BM < (bj + 1) * TC_BN; ++bi) t.push_back(make_int2(bi, bj));
-    }
+// CTA b takes tiles b, b + grid, ..., so each run of `grid` consecutive tiles is
+// in flight together.  Tiles are ordered by 2048 x 2048 super-blocks (column
+// super-block, then row super-block, then column, then row) so that such a run
+// reads a compact set of row and column panels and the operand matrices, which
+// are larger than L2, are fetched from HBM about once per run.
+void build_tiles(int path, int np, int cg, std::vector<int2> &t) {
+    const int bm = (path == PATH_SIMT) ? SIMT_T : TC_BM * cg;
+    const int bn = (path == PATH_SIMT) ? SIMT_T : TC_BN;
+    const int nbi = (np + bm - 1) / bm, nbj = (np + bn - 1) / bn;  // a last pair tile may overhang np
+    const int sbi = 2048 / bm, sbj = 2048 / bn;  // tiles per super-block side
+    std::vector<std::pair<long long, int2>> keyed;
+    for (int bj = 0; bj < nbj; ++bj)
+        for (int bi = 0; bi < nbi && bi * bm < (bj + 1) * bn; ++bi) {
+            const long long key = (((long long)(bj / sbj) * 4096 + bi / sbi) * 4096 + bj) * 4096 + bi;
+            keyed.push_back({key, make_int2(bi, bj)});
+        }
+    std::sort(keyed.begin(), keyed.end(), [](const std::pair<long long, int2> &a, const std::pair<long long, int2> &b) {
+        return a.first < b.first;
+    });
+    for (auto &k : keyed) t.push_back(k.second);
 }
 
-int ntiles_for(int path, int np) {
+int ntiles_for(int path, int np, int cg) {
     std::vector<int2> t;
-    build_tiles(path, np, t);
+    build_tiles(path, np, cg, t);
     return (int)t.size();
 }
+
+// Partial records per layer: one per tile, per CTA of the tile.
+int parts_for(int path, int np, int cg) { return ntiles_for(path, np, cg) * (path == PATH_TC ? cg : 1); }
 
 // Must equal the device-side init_blocks_for: one partial per input-layer block.
 int init_blocks_host(int np) { return np < INIT_BLOCKS_MAX ? np : INIT_BLOCKS_MAX; }
 
 struct Plan {
     int mode, path, precision;
+    int cg = 1;                       // CTAs per tensor-core tile
     std::vector<InstSpec> inst;       // non-trivial instances, in launch order
     std::vector<int> slots;           // nslots_x per instance
     int max_np = 0, max_n = 0;
@@ -169,7 +183,7 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
     const int B = (int)pl.inst.size();
     c.take(sizeof(InstDesc) * B);
     int tiles = 0;
-    for (auto &s : pl.inst) tiles += ntiles_for(pl.path, round_up(s.n, PAD));
+    for (auto &s : pl.inst) tiles += ntiles_for(pl.path, round_up(s.n, PAD), pl.cg);
     c.take(sizeof(int2) * tiles);
     c.take(64);                           // barrier + err
     c.take(sizeof(int) * (MAX_L + 1));    // forced choices
@@ -177,8 +191,7 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
     for (int i = 0; i < B; ++i) {
         const int np = round_up(pl.inst[i].n, PAD);
         const size_t mat = (size_t)np * np;
-        const int nt = ntiles_for(pl.path, np);
-        const int cap = std::max(nt, initb);
+        const int cap = std::max(parts_for(pl.path, np, pl.cg), initb);
         c.take(sizeof(InstCtl));
         c.take(sizeof(Part) * cap);
         c.take(sizeof(Part) * cap);
@@ -259,6 +272,26 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     if (di.err != cudaSuccess) return SP2_ERR_CUDA;
     if (di.major != 10 || di.minor != 3) return SP2_ERR_UNSUPPORTED;
     if (pl.path == PATH_TC && !get_encode_fn()) return SP2_ERR_UNSUPPORTED;
+    // Tensor-core tile shape: CTA pairs (M = 256) when the device can co-schedule
+    // them for a cooperative launch, else single CTAs.
+    int grid = 0;
+    if (pl.path == PATH_TC) {
+        const int want = o.cta_group;
+        if (want == 0 || want == 2) {
+            grid = tc_grid_size(2, di.sm);
+            pl.cg = 2;
+        }
+        if (grid <= 0) {
+            if (want == 2) return SP2_ERR_UNSUPPORTED;
+            grid = tc_grid_size(1, di.sm);
+            pl.cg = 1;
+        }
+        if (grid <= 0) return SP2_ERR_UNSUPPORTED;
+    } else {
+        const int per_sm = simt_blocks_per_sm();
+        if (per_sm <= 0) return SP2_ERR_UNSUPPORTED;
+        grid = per_sm * di.sm;
+    }
 
     Arena arena(s);
     const size_t need = plan_bytes(pl);
@@ -273,7 +306,7 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     std::vector<std::vector<int2>> tiles(B);
     int total_tiles = 0;
     for (int i = 0; i < B; ++i) {
-        build_tiles(pl.path, round_up(pl.inst[i].n, PAD), tiles[i]);
+        build_tiles(pl.path, round_up(pl.inst[i].n, PAD), pl.cg, tiles[i]);
         total_tiles += (int)tiles[i].size();
     }
     int2 *d_tiles = (int2 *)c.take(sizeof(int2) * total_tiles);
@@ -299,12 +332,13 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
         d.n = n;
         d.np = np;
         d.ntiles = (int)tiles[i].size();
+        d.parts = d.ntiles * (pl.path == PATH_TC ? pl.cg : 1);
         d.tile_off = (int)h_tiles.size();
         h_tiles.insert(h_tiles.end(), tiles[i].begin(), tiles[i].end());
         d.n_occ = sp.n_occ;
         d.nforced = -1;
         d.nslots_x = pl.slots[i];
-        d.part_cap = std::max(d.ntiles, initb);
+        d.part_cap = std::max(d.parts, initb);
         d.fin_blocks = FIN_BLOCKS_MAX;
         d_ctl[i] = (InstCtl *)c.take(sizeof(InstCtl));
         d.ctl = d_ctl[i];
@@ -475,12 +509,8 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     rp.precision = pl.precision;
     rp.max_layers = o.max_layers;
     rp.test_hook = o.test_hook;
-    int per_sm = (pl.path == PATH_TC) ? tc_blocks_per_sm() : simt_blocks_per_sm();
-    if (per_sm <= 0) return SP2_ERR_UNSUPPORTED;
-    if (pl.path == PATH_TC) per_sm = 1;
-    const int grid = per_sm * di.sm;
     if (o.profile) CK(cudaEventRecord(ev[1], s));
-    CK(pl.path == PATH_TC ? launch_tc_persistent(rp, grid, s) : launch_simt_persistent(rp, grid, s));
+    CK(pl.path == PATH_TC ? launch_tc_persistent(rp, pl.cg, grid, s) : launch_simt_persistent(rp, grid, s));
     if (o.profile) CK(cudaEventRecord(ev[2], s));
 
     CK(launch_finalize(d_inst, B, pl.max_n, pl.mode == MODE_APPLY ? MODE_DENSITY : pl.mode, s));
@@ -503,8 +533,10 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     int worst = SP2_OK;
     for (int i = 0; i < B; ++i) {
         fill_stats(pl.inst[i].st, h_ctl[i]);
-        if (pl.inst[i].st)
+        if (pl.inst[i].st) {
             for (int k = 0; k < 4; ++k) pl.inst[i].st->phase_ms[k] = ph[k];
+            pl.inst[i].st->cta_group = (pl.path == PATH_TC) ? pl.cg : 0;
+        }
         int stt = h_ctl[i].status;
         if (h_ctl[i].nonfinite) stt = SP2_ERR_NONFINITE;
         if (status_rank(stt) > status_rank(worst)) worst = stt;
@@ -523,6 +555,7 @@ sp2_status check_opts(const sp2_opts &o) {
     if (o.user_bounds && !(o.eps_max > o.eps_min)) return SP2_ERR_ARG;
     if (o.test_hook < 0 || o.test_hook > 1) return SP2_ERR_ARG;
     if (o.profile < 0 || o.profile > 1) return SP2_ERR_ARG;
+    if (o.cta_group < 0 || o.cta_group > 2) return SP2_ERR_ARG;
     return SP2_OK;
 }
 
@@ -630,7 +663,11 @@ size_t bytes_for(int mode, const std::vector<int> &ns, int layers, const sp2_opt
         pl.max_np = std::max(pl.max_np, round_up(n, PAD));
     }
     if (pl.inst.empty()) return 0;
-    return plan_bytes(pl);
+    pl.cg = 1;
+    const size_t b1 = plan_bytes(pl);
+    pl.cg = 2;
+    const size_t b2 = plan_bytes(pl);
+    return b1 > b2 ? b1 : b2;  // the tile shape is chosen per device at run time
 }
 
 }  // namespace

@@ -196,7 +196,7 @@ __device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams
         if (!rc.active[i]) continue;
         const InstDesc &d = p.inst[i];
         const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
-        const int cnt = (n == 0) ? d.ctl->init_parts : d.ntiles;
+        const int cnt = (n == 0) ? d.ctl->init_parts : d.parts;
         const Part *part = d.part[n & 1];
         double a[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 4

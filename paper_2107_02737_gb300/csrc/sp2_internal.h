@@ -70,6 +70,8 @@ struct InstCtl {
 
 struct InstDesc {
     int n, np, ntiles, tile_off;      // tiles: this instance's slice of the tile table
+    int parts;                        // partial records per layer (tiles x CTAs per tile)
+    int pad_parts;
     double n_occ;
     int nforced, nslots_x;            // nforced < 0: decide on device; nslots_x: 2 or L+1
     const int *forced;                // replayed layer choices (device)
@@ -110,9 +112,9 @@ cudaError_t launch_init_y(InstDesc *inst, int mode, int precision, cudaStream_t 
 cudaError_t launch_finalize(InstDesc *inst, int B, int max_n, int mode, cudaStream_t s);
 cudaError_t launch_fill_trivial(float *D, int n, float diag_value, cudaStream_t s);
 cudaError_t launch_simt_persistent(const RunParams &p, int grid, cudaStream_t s);
-cudaError_t launch_tc_persistent(const RunParams &p, int grid, cudaStream_t s);
+cudaError_t launch_tc_persistent(const RunParams &p, int cta_group, int grid, cudaStream_t s);
 int simt_blocks_per_sm();
-int tc_blocks_per_sm();
+int tc_grid_size(int cta_group, int sm_count);
 size_t tc_smem_bytes();
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }

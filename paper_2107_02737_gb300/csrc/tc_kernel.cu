@@ -38,16 +38,27 @@ namespace sp2i {
 
 namespace {
 
-constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;           // 16 KB
-constexpr uint32_t B_BYTES = TC_BN * TC_BK * 2;           // 32 KB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;       // 48 KB
+// Tile configuration.  CG = 1: one CTA computes a 128 x 256 tile (M = 128 MMAs).
+// CG = 2: a cluster of two CTAs computes a 256 x 256 tile with M = 256 MMAs
+// issued by the even CTA; each CTA loads its own 128 rows of A and 128 of the
+// 256 B rows, so a stage is 32 KB per CTA and six stages fit.
+template <int CG>
+struct Cfg {
+    static constexpr int STAGES = (CG == 2) ? 6 : 4;
+    static constexpr uint32_t A_BYTES = 128 * TC_BK * 2;                   // 16 KB: own 128 rows
+    static constexpr uint32_t B_BYTES = (CG == 2 ? 128 : 256) * TC_BK * 2;  // own B rows
+    static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t TX_BYTES = STAGE_BYTES * CG;               // bytes per stage over the pair
+    static constexpr int TILE_M = 128 * CG;                              // output rows per tile
+};
+constexpr int MAX_STAGES = 6;
 constexpr uint32_t EPI_T_FLOATS = 32 * 33;                // transpose buffer per epilogue warp
 constexpr uint32_t TMEM_COLS = 512;                       // two 128 x 256 FP32 accumulators
 constexpr int EPI_WARPS = 4;
 
 struct TcSmemTail {
-    uint64_t full[TC_STAGES];
-    uint64_t empty[TC_STAGES];
+    uint64_t full[MAX_STAGES];
+    uint64_t empty[MAX_STAGES];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint32_t tmem_base;
@@ -56,8 +67,11 @@ struct TcSmemTail {
     RoundCtl rc;
 };
 
-constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)TC_STAGES * STAGE_BYTES +
-                              (size_t)EPI_WARPS * EPI_T_FLOATS * 4 + sizeof(TcSmemTail);
+constexpr size_t STAGE_AREA = 196608;  // 4 x 48 KB or 6 x 32 KB
+static_assert(Cfg<1>::STAGES * Cfg<1>::STAGE_BYTES <= STAGE_AREA, "stage area");
+static_assert(Cfg<2>::STAGES * Cfg<2>::STAGE_BYTES <= STAGE_AREA, "stage area");
+constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGE_AREA + (size_t)EPI_WARPS * EPI_T_FLOATS * 4 +
+                              sizeof(TcSmemTail);
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -120,22 +134,70 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, A and B of one 16-bit
-// type (0 = FP16, 1 = BF16), both K-major, N = 256, M = 128.
-__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab) {
-    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+// type (0 = FP16, 1 = BF16), both K-major, N = 256, M = 128 * CG.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab, int m) {
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+template <int CG>
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if (CG == 2)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
 }
+// Arrive on `bar` once the MMAs issued so far have completed; for a CTA pair the
+// arrival goes to the barrier at the same offset in both CTAs.
+template <int CG>
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    if (CG == 2) {
+        const uint16_t both = 3;
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                smem_u32(bar)),
+            "h"(both)
+            : "memory");
+    } else {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Shared::cluster address of `p` in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on the
+// barrier at `cluster_bar` (the even CTA's barrier of a CTA pair).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t cluster_bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(cluster_bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -220,48 +282,69 @@ __device__ __forceinline__ void segment_maps(const InstDesc &d, const TileWork &
     }
 }
 
-template <int PREC>
+template <int PREC, int CG>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_constant__ RunParams p) {
+    using C = Cfg<CG>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *stages = smem;
-    float *epi_T = (float *)(smem + (size_t)TC_STAGES * STAGE_BYTES);
+    float *epi_T = (float *)(smem + STAGE_AREA);
     TcSmemTail &tl = *(TcSmemTail *)(epi_T + EPI_WARPS * EPI_T_FLOATS);
     RoundCtl &rc = tl.rc;
     const volatile int *abort = &rc.abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = (CG == 2) ? cluster_rank() : 0u;   // position in the CTA pair
+    const bool leader = (rank == 0);
+    const int cluster_id = blockIdx.x / CG, nclusters = gridDim.x / CG;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&tl.full[s], 1);
             mbar_init(&tl.empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tl.tfull[a], 1);
-            mbar_init(&tl.tempty[a], EPI_WARPS * 32);
+            mbar_init(&tl.tempty[a], EPI_WARPS * CG);  // one arrival per epilogue warp of the pair
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         round_ctl_init(rc, p);
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tl.tmem_base)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (CG == 2) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tl.tmem_base)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tl.tmem_base)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
         tc_fence_before();
     }
     __syncthreads();
+    if (CG == 2) cluster_sync_all();  // both CTAs' barriers exist before any cross-CTA signal
     tc_fence_after();
     const uint32_t tmem_base = tl.tmem_base;
+
+    // Cluster addresses of the even CTA's barriers (the pair's MMA side).
+    uint32_t lead_full0 = 0, lead_tempty0 = 0;
+    if (CG == 2) {
+        lead_full0 = cluster_addr(&tl.full[0], 0);
+        lead_tempty0 = cluster_addr(&tl.tempty[0], 0);
+    }
 
     // Pipeline state, private to each role and carried across tiles and rounds.
     uint32_t stage = 0, phase = 0;      // producer / MMA ring
     uint32_t acc = 0, acc_phase = 0;    // MMA / epilogue accumulators
-    int pend[TC_STAGES];                // producer: parity + 1 of a load not yet released
-    for (int s = 0; s < TC_STAGES; ++s) pend[s] = 0;
-    const uint32_t idesc = idesc_f16(PREC == SP2_BF16_SPLIT ? 1u : 0u);
+    int pend[MAX_STAGES];               // producer: parity + 1 of a load not yet released
+    for (int s = 0; s < MAX_STAGES; ++s) pend[s] = 0;
+    const uint32_t idesc = idesc_f16(PREC == SP2_BF16_SPLIT ? 1u : 0u, C::TILE_M);
     const float unscale = split_unscale<PREC>();
 
     unsigned int target = 0;
@@ -292,11 +375,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         if (warp == 0) {
             // ------------------------- TMA producer -------------------------
             if (lane == 0) {
-                for (int g = blockIdx.x; g < rc.total && !*abort; g += gridDim.x) {
+                for (int g = cluster_id; g < rc.total && !*abort; g += nclusters) {
                     const TileWork w = describe(rc, p, g);
                     const InstDesc &d = p.inst[w.inst];
                     const int nkb = d.np / TC_BK;
                     const int nseg = w.resp ? 6 : 3;
+                    const int row_a = w.bi * C::TILE_M + (int)rank * 128;
+                    const int row_b = w.bj * TC_BN + (CG == 2 ? (int)rank * 128 : 0);
                     for (int kb = 0; kb < nseg * nkb; ++kb) {
                         const int s = kb / nkb;
                         const int kx = (kb - s * nkb) * TC_BK;
@@ -307,13 +392,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             break;
                         }
                         pend[stage] = 0;
-                        uint8_t *sa = stages + (size_t)stage * STAGE_BYTES;
-                        mbar_expect_tx(&tl.full[stage], STAGE_BYTES);
-                        tma_load_2d(sa, am, kx, w.bi * TC_BM, &tl.full[stage]);
-                        tma_load_2d(sa + A_BYTES, bm, kx, w.bj * TC_BN, &tl.full[stage]);
-                        tma_load_2d(sa + A_BYTES + B_BYTES / 2, bm, kx, w.bj * TC_BN + TC_BN / 2, &tl.full[stage]);
+                        uint8_t *sa = stages + (size_t)stage * C::STAGE_BYTES;
+                        if (CG == 1) {
+                            mbar_expect_tx(&tl.full[stage], C::TX_BYTES);
+                            tma_load_2d(sa, am, kx, row_a, &tl.full[stage]);
+                            tma_load_2d(sa + C::A_BYTES, bm, kx, row_b, &tl.full[stage]);
+                            tma_load_2d(sa + C::A_BYTES + C::B_BYTES / 2, bm, kx, row_b + 128, &tl.full[stage]);
+                        } else {
+                            // Both CTAs' bytes complete on the even CTA's barrier.
+                            if (leader) mbar_expect_tx(&tl.full[stage], C::TX_BYTES);
+                            const uint32_t fb = lead_full0 + stage * 8u;
+                            tma_load_2d_pair(sa, am, kx, row_a, fb);
+                            tma_load_2d_pair(sa + C::A_BYTES, bm, kx, row_b, fb);
+                        }
                         pend[stage] = (int)phase + 1;
-                        if (++stage == TC_STAGES) {
+                        if (++stage == C::STAGES) {
                             stage = 0;
                             phase ^= 1u;
                         }
@@ -322,8 +415,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             }
         } else if (warp == 1) {
             // -------------------------- MMA issuer --------------------------
-            if (lane == 0) {
-                for (int g = blockIdx.x; g < rc.total && !*abort; g += gridDim.x) {
+            if (lane == 0 && leader) {
+                for (int g = cluster_id; g < rc.total && !*abort; g += nclusters) {
                     const TileWork w = describe(rc, p, g);
                     const InstDesc &d = p.inst[w.inst];
                     const int nkb = (d.np / TC_BK) * (w.resp ? 6 : 3);
@@ -341,20 +434,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = smem_u32(stages + (size_t)stage * STAGE_BYTES);
-                        const uint32_t sb = sa + A_BYTES;
+                        const uint32_t sa = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                        const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
                         for (int k = 0; k < TC_BK / 16; ++k) {
-                            umma_f16(d_tmem, sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
-                                     (kb | k) != 0 ? 1u : 0u);
+                            umma_f16<CG>(d_tmem, sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
+                                         (kb | k) != 0 ? 1u : 0u);
                         }
-                        umma_commit(&tl.empty[stage]);
-                        if (++stage == TC_STAGES) {
+                        umma_commit<CG>(&tl.empty[stage]);
+                        if (++stage == C::STAGES) {
                             stage = 0;
                             phase ^= 1u;
                         }
                     }
-                    umma_commit(&tl.tfull[acc]);
+                    umma_commit<CG>(&tl.tfull[acc]);
                     if (++acc == 2) {
                         acc = 0;
                         acc_phase ^= 1u;
@@ -367,7 +460,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             const int ew = warp - 2;
             const int quarter = warp & 3;             // TMEM lanes this warp may access
             float *T = epi_T + ew * EPI_T_FLOATS;
-            for (int g = blockIdx.x; g < rc.total; g += gridDim.x) {
+            for (int g = cluster_id; g < rc.total; g += nclusters) {
                 const TileWork w = describe(rc, p, g);
                 const InstDesc &d = p.inst[w.inst];
                 const int np = d.np;
@@ -376,9 +469,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 if (lane == 0) ok = mbar_wait(&tl.tfull[acc], acc_phase, abort, p.timeout_ns, p.err) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 tc_fence_after();
-                const float *old;
-                float *outf;
-                uint16_t *o0, *o1, *o2;
+                const float *__restrict__ old;
+                float *__restrict__ outf;
+                uint16_t *__restrict__ o0;
+                uint16_t *__restrict__ o1;
+                uint16_t *__restrict__ o2;
                 bool write0;
                 if (!w.resp) {
                     old = d.xf[w.n & 1];
@@ -398,24 +493,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     o2 = base + 2 * mat;
                     write0 = false;
                 }
-                const int rw0 = w.bi * TC_BM + quarter * 32;  // first row of this warp
+                const int rw0 = w.bi * C::TILE_M + (int)rank * 128 + quarter * 32;  // first row of this warp
                 const int r = rw0 + lane;
                 const int nreal = d.n;
                 const float cf = w.cf;
                 FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f}, fp = {0.f, 0.f};
-                if (ok) {
+                if (ok && rw0 < np) {
 #pragma unroll 1
                     for (int j = 0; j < TC_BN / 32; ++j) {
                         const int cb = w.bj * TC_BN + j * 32;
                         if (cb >= np) break;
                         if (cb + 31 < rw0) continue;  // chunk entirely below the diagonal
+                        // All 32 loads of the previous layer's (r, c) values are issued
+                        // before any store of this chunk: (c, r) by symmetry, coalesced
+                        // across the warp, evict-first.
+                        float xov[32];
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) xov[jj] = __ldcs(old + (size_t)(cb + jj) * np + r);
                         float v[32];
                         tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + j * 32, v);
 #pragma unroll
                         for (int jj = 0; jj < 32; ++jj) {
                             const int c = cb + jj;
                             const float P = v[jj] * unscale;            // raw product
-                            const float xo = old[(size_t)c * np + r];   // (r, c) by symmetry, coalesced
+                            const float xo = xov[jj];
                             const bool dg = (r == c) && (r < nreal);
                             float x;
                             if (!w.resp) {
@@ -441,12 +542,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 }
                                 if (r < c) {  // mirror (c, r): consecutive r across the warp
                                     const size_t m = (size_t)c * np + r;
-                                    outf[m] = x;
+                                    __stcs(outf + m, x);   // streaming stores: keep L2 for the operands
                                     uint16_t a0, a1, a2;
                                     split3<PREC>(y, a0, a1, a2);
-                                    if (write0) o0[m] = a0;
-                                    o1[m] = a1;
-                                    o2[m] = a2;
+                                    if (write0) __stcs(o0 + m, a0);
+                                    __stcs(o1 + m, a1);
+                                    __stcs(o2 + m, a2);
                                 }
                             }
                             T[lane * 33 + jj] = x;
@@ -460,19 +561,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 const float x = T[ii * 33 + lane];
                                 const float y = (rr == cc && rr < nreal && !w.resp) ? x - 0.5f : x;
                                 const size_t m = (size_t)rr * np + cc;
-                                outf[m] = x;
+                                __stcs(outf + m, x);
                                 uint16_t a0, a1, a2;
                                 split3<PREC>(y, a0, a1, a2);
-                                if (write0) o0[m] = a0;
-                                o1[m] = a1;
-                                o2[m] = a2;
+                                if (write0) __stcs(o0 + m, a0);
+                                __stcs(o1 + m, a1);
+                                __stcs(o2 + m, a2);
                             }
                         }
                         __syncwarp();
                     }
                 }
+                // Release the accumulator: every lane's loads have completed
+                // (tcgen05.wait::ld); one arrival per warp on the MMA side's barrier.
                 tc_fence_before();
-                mbar_arrive(&tl.tempty[acc]);
+                __syncwarp();
+                if (lane == 0) {
+                    if (CG == 2) mbar_arrive_cluster(lead_tempty0 + acc * 8u);
+                    else mbar_arrive(&tl.tempty[acc]);
+                }
                 if (++acc == 2) {
                     acc = 0;
                     acc_phase ^= 1u;
@@ -494,7 +601,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             s4.w += tl.red[k][2];
                             s4.p += tl.red[k][3];
                         }
-                        d.part[(w.n + 1) & 1][w.tile] = s4;
+                        d.part[(w.n + 1) & 1][w.tile * CG + (int)rank] = s4;
                     }
                     asm volatile("bar.sync 1, 128;" ::: "memory");
                 }
@@ -507,9 +614,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     }
 
     // ------------------------------ teardown ------------------------------
-    if (warp == 0 && lane == 0 && rc.abort) {
-        // Let loads still in flight land before the CTA exits (bounded wait).
-        for (int s = 0; s < TC_STAGES; ++s) {
+    if (warp == 0 && lane == 0 && rc.abort && leader) {
+        // Let loads still in flight land before the CTA (pair) exits: bounded
+        // waits on the barriers that count them (the even CTA's for a pair).
+        for (int s = 0; s < C::STAGES; ++s) {
             if (pend[s]) {
                 const unsigned long long t0 = global_ns();
                 while (!mbar_try_wait(&tl.full[s], (uint32_t)(pend[s] - 1)) && global_ns() - t0 < 50000000ull) {
@@ -517,37 +625,94 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             }
         }
     }
+    if (CG == 2 && rc.abort && threadIdx.x == 0) {
+        // The odd CTA's loads complete on its peer's barriers, which it cannot
+        // wait on: give any copy still in flight time to land (bounded, 1 ms).
+        const unsigned long long t0 = global_ns();
+        while (global_ns() - t0 < 1000000ull) {
+        }
+    }
     __syncthreads();
+    if (CG == 2) cluster_sync_all();  // neither CTA leaves while its peer may still signal it
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
-                     : "memory");
+        if (CG == 2)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                         : "memory");
     }
+}
+
+template <int CG>
+const void *tc_kernel_ptr(int precision) {
+    return (precision == SP2_BF16_SPLIT) ? (const void *)k_tc_persistent<SP2_BF16_SPLIT, CG>
+                                         : (const void *)k_tc_persistent<SP2_FP16_SPLIT, CG>;
 }
 
 }  // namespace
 
 size_t tc_smem_bytes() { return SMEM_BYTES; }
 
-int tc_blocks_per_sm() {
-    int b = 0;
-    if (cudaFuncSetAttribute(k_tc_persistent<SP2_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES) != cudaSuccess)
+// Number of CTAs of a co-resident persistent grid for the given CTA group size
+// (0 when the configuration cannot be launched on this device).
+int tc_grid_size(int cta_group, int sm_count) {
+    const void *fns[2] = {cta_group == 2 ? tc_kernel_ptr<2>(SP2_FP16_SPLIT) : tc_kernel_ptr<1>(SP2_FP16_SPLIT),
+                          cta_group == 2 ? tc_kernel_ptr<2>(SP2_BF16_SPLIT) : tc_kernel_ptr<1>(SP2_BF16_SPLIT)};
+    for (const void *f : fns)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+    if (cta_group == 1) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[0], TC_THREADS, SMEM_BYTES) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return b >= 1 ? sm_count : 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(sm_count);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fns[0], &cfg) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
-    if (cudaFuncSetAttribute(k_tc_persistent<SP2_BF16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tc_persistent<SP2_FP16_SPLIT>, TC_THREADS, SMEM_BYTES) !=
-        cudaSuccess)
-        return 0;
-    return b;
+    }
+    if (nclusters * 2 > sm_count) nclusters = sm_count / 2;
+    return nclusters * 2;
 }
 
-cudaError_t launch_tc_persistent(const RunParams &p, int grid, cudaStream_t s) {
+cudaError_t launch_tc_persistent(const RunParams &p, int cta_group, int grid, cudaStream_t s) {
     void *args[] = {(void *)&p};
-    const void *fn = (p.precision == SP2_BF16_SPLIT) ? (const void *)k_tc_persistent<SP2_BF16_SPLIT>
-                                                     : (const void *)k_tc_persistent<SP2_FP16_SPLIT>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(TC_THREADS), args, SMEM_BYTES, s);
+    if (cta_group == 1)
+        return cudaLaunchCooperativeKernel(tc_kernel_ptr<1>(p.precision), dim3(grid), dim3(TC_THREADS), args,
+                                           SMEM_BYTES, s);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelExC(&cfg, tc_kernel_ptr<2>(p.precision), args);
 }
 
 }  // namespace sp2i

@@ -36,14 +36,14 @@ class LayerStat(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("layers", ctypes.c_int), ("stop_reason", ctypes.c_int), ("eps_min", ctypes.c_double),
                 ("eps_max", ctypes.c_double), ("band_energy", ctypes.c_double), ("trace_D", ctypes.c_double),
-                ("layer", ctypes.POINTER(LayerStat)), ("layer_cap", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("layer", ctypes.POINTER(LayerStat)), ("layer_cap", ctypes.c_int), ("cta_group", ctypes.c_int),
                 ("phase_ms", ctypes.c_float * 4)]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_layers", ctypes.c_int), ("timeout_ms", ctypes.c_double),
                 ("user_bounds", ctypes.c_int), ("test_hook", ctypes.c_int), ("eps_min", ctypes.c_double),
-                ("eps_max", ctypes.c_double), ("profile", ctypes.c_int), ("reserved2", ctypes.c_int)]
+                ("eps_max", ctypes.c_double), ("profile", ctypes.c_int), ("cta_group", ctypes.c_int)]
 
 
 EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
@@ -121,6 +121,7 @@ class Result:
     choices: List[int]          # choice that produced X_n, n = 1..layers
     raw: Stats = dataclasses.field(repr=False, default=None)
     phase_ms: List[float] = dataclasses.field(default_factory=list)
+    cta_group: int = 0
 
     @property
     def converged(self) -> bool:
@@ -128,7 +129,7 @@ class Result:
 
 
 def make_opts(precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0,
-              bounds: Optional[Sequence[float]] = None, profile: bool = False) -> Opts:
+              bounds: Optional[Sequence[float]] = None, profile: bool = False, cta_group: int = 0) -> Opts:
     o = Opts()
     load().sp2_default_opts(ctypes.byref(o))
     if precision not in PRECISIONS:
@@ -140,6 +141,7 @@ def make_opts(precision: str = "fp16", max_layers: int = 100, timeout_ms: float 
         o.user_bounds = 1
         o.eps_min, o.eps_max = float(bounds[0]), float(bounds[1])
     o.profile = 1 if profile else 0
+    o.cta_group = int(cta_group)
     return o
 
 
@@ -157,7 +159,7 @@ def _result(status: int, st: Stats) -> Result:
     lay = [st.layer[k] for k in range(n)]
     return Result(status, st.layers, st.stop_reason, st.eps_min, st.eps_max, st.band_energy, st.trace_D,
                   [l.trace for l in lay], [l.trace_sq for l in lay], [l.idem for l in lay],
-                  [l.choice for l in lay[1:]], st, list(st.phase_ms))
+                  [l.choice for l in lay[1:]], st, list(st.phase_ms), st.cta_group)
 
 
 def _check(status: int, where: str):
@@ -204,13 +206,16 @@ def workspace_bytes(n: int, kind: str = "density", precision: str = "fp16", laye
 
 def density(H: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16", max_layers: int = 100,
             timeout_ms: float = 2000.0, bounds=None, out: Optional[torch.Tensor] = None,
-            workspace: Optional[torch.Tensor] = None, stream=None, profile: bool = False):
-    """D = theta(mu I - H) by the DNN-SP2 chain; returns (D, Result)."""
+            workspace: Optional[torch.Tensor] = None, stream=None, profile: bool = False, cta_group: int = 0):
+    """D = theta(mu I - H) by the DNN-SP2 chain; returns (D, Result).
+
+    ``cta_group`` selects the tensor-core tile shape (0 = library's choice, 1 or 2).
+    """
     H = _f64(H, "H")
     n = _square(H, "H")
     D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms, bounds, profile)
+    o = make_opts(precision, max_layers, timeout_ms, bounds, profile, cta_group)
     ws, wsb = _ws_args(workspace)
     s = load().sp2_density(ctypes.c_void_p(H.data_ptr()), n, float(n_occ), float(tol), ctypes.c_void_p(D.data_ptr()),
                            ctypes.byref(st), ctypes.byref(o), ws, wsb, ctypes.c_void_p(_stream_handle(H, stream)))
@@ -290,7 +295,7 @@ def density_batched(Hs: Sequence[torch.Tensor], n_occs: Sequence[int], tol: floa
 
 
 def apply_layers(X0: torch.Tensor, choices: Sequence[int], precision: str = "fp16", timeout_ms: float = 2000.0,
-                 stream=None):
+                 stream=None, cta_group: int = 0):
     """Apply the given layer signs to X0 (float32, symmetric); returns (X, Result)."""
     if X0.dtype != torch.float32:
         raise TypeError("X0 must be float32")
@@ -298,7 +303,7 @@ def apply_layers(X0: torch.Tensor, choices: Sequence[int], precision: str = "fp1
     n = _square(X0, "X0")
     X = torch.empty_like(X0)
     st = _new_stats()
-    o = make_opts(precision, MAX_LAYERS_LIMIT, timeout_ms)
+    o = make_opts(precision, MAX_LAYERS_LIMIT, timeout_ms, cta_group=cta_group)
     ch = (ctypes.c_int * max(1, len(choices)))(*[int(c) for c in choices])
     s = load().sp2_apply_layers(ctypes.c_void_p(X0.data_ptr()), n, ch, len(choices), ctypes.c_void_p(X.data_ptr()),
                                 ctypes.byref(st), ctypes.byref(o), ctypes.c_void_p(_stream_handle(X0, stream)))

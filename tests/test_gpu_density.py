@@ -82,11 +82,11 @@ def test_layer_statistics_match_oracle_replay(c0, precision):
     assert k >= 10
 
 
-@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("precision,cg", [("fp32", 0), ("fp16", 1), ("fp16", 2), ("bf16", 1), ("bf16", 2)])
 @pytest.mark.parametrize("n", [300, 1000])
-def test_ragged_sizes(precision, n):
+def test_ragged_sizes(precision, cg, n):
     ham = inputs.gapped_random(n, n // 3, inputs.rng_for(0, n))
-    D, res = sp2.density(dev(ham.H), ham.n_occ, precision=precision)
+    D, res = sp2.density(dev(ham.H), ham.n_occ, precision=precision, cta_group=cg)
     Dh = host(D)
     ref = odens.density_from_eigensystem(ham.eigvecs, ham.n_occ)
     assert res.converged
@@ -155,9 +155,9 @@ def test_user_bounds(c0, precision):
     assert res.layers < rg.layers  # tight bounds need fewer layers
 
 
-def _full_size_checks(ham, precision, rows=8):
+def _full_size_checks(ham, precision, rows=8, cta_group=0):
     H = dev(ham.H)
-    D, res = sp2.density(H, ham.n_occ, precision=precision)
+    D, res = sp2.density(H, ham.n_occ, precision=precision, cta_group=cta_group)
     torch.cuda.synchronize()
     n = ham.n
     assert res.converged
@@ -186,6 +186,10 @@ def c1_4096():
 @pytest.mark.parametrize("precision", ["fp16", "fp32"])
 def test_full_size_4096(c1_4096, precision):
     _full_size_checks(c1_4096, precision)
+
+
+def test_full_size_4096_single_cta_tiles(c1_4096):
+    _full_size_checks(c1_4096, "fp16", cta_group=1)
 
 
 def test_full_size_8192_fp16():

@@ -22,12 +22,16 @@ def start_matrix(n, seed):
     return osp2.input_layer(ham.H, lo, hi).astype(np.float32)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+# (precision, CTAs per tensor-core tile): the FP32 path ignores the tile shape.
+PATHS = [("fp32", 0), ("fp16", 1), ("fp16", 2), ("bf16", 1), ("bf16", 2)]
+
+
+@pytest.mark.parametrize("precision,cg", PATHS)
 @pytest.mark.parametrize("n", [256, 300, 640])
 @pytest.mark.parametrize("choice", [0, 1])
-def test_one_layer_matches_fp64_product(precision, n, choice):
+def test_one_layer_matches_fp64_product(precision, cg, n, choice):
     X0 = start_matrix(n, 100 + n)
-    X, res = sp2.apply_layers(dev(X0, torch.float32), [choice], precision=precision)
+    X, res = sp2.apply_layers(dev(X0, torch.float32), [choice], precision=precision, cta_group=cg)
     got = host(X)
     x = X0.astype(np.float64)
     ref = osp2.apply_layer(x, choice)
@@ -46,12 +50,12 @@ def test_one_layer_matches_fp64_product(precision, n, choice):
     assert res.trace_sq[0] == pytest.approx(np.sum(x * x), rel=1e-12)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
-def test_layer_sequence_matches_replay(precision):
+@pytest.mark.parametrize("precision,cg", PATHS)
+def test_layer_sequence_matches_replay(precision, cg):
     n = 384
     X0 = start_matrix(n, 7)
     choices = [0, 1, 1, 0, 1]
-    X, res = sp2.apply_layers(dev(X0, torch.float32), choices, precision=precision)
+    X, res = sp2.apply_layers(dev(X0, torch.float32), choices, precision=precision, cta_group=cg)
     x = X0.astype(np.float64)
     for c in choices:
         x = osp2.apply_layer(x, c)
@@ -66,6 +70,15 @@ def test_deterministic(precision):
     b, rb = sp2.apply_layers(X0, [0, 1, 0], precision=precision)
     assert torch.equal(a, b)
     assert ra.trace == rb.trace and ra.trace_sq == rb.trace_sq
+
+
+def test_tile_shapes_agree():
+    # 128 x 256 single-CTA tiles and 256 x 256 CTA-pair tiles: same products,
+    # different accumulation splits, so agreement within the split tolerance.
+    X0 = dev(start_matrix(640, 11), torch.float32)
+    a, _ = sp2.apply_layers(X0, [0, 1], precision="fp16", cta_group=1)
+    b, _ = sp2.apply_layers(X0, [0, 1], precision="fp16", cta_group=2)
+    assert float((a - b).abs().max()) < 2 * TOL_SQ["fp16"]
 
 
 def test_zero_layers_returns_input():
