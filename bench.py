@@ -123,6 +123,46 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SOURCES = ["paper_2107_02737_gb300/csrc/tc_kernel.cu", "paper_2107_02737_gb300/csrc/device_common.cuh",
+                  "paper_2107_02737_gb300/csrc/sp2_internal.h"]
+
+
+def kernel_source_sha():
+    """First 16 hex digits of the SHA-256 of the persistent kernel's sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n, layers, precision):
+    """DRAM bytes per launch of the persistent kernel from a committed ncu summary
+    (profiles/*.md lines 'key: value'), only when it was taken on the current
+    kernel sources with the same size, layer count and precision; else None."""
+    sha = kernel_source_sha()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for f in sorted(os.listdir(pdir)):
+        if not f.endswith(".md"):
+            continue
+        kv = {}
+        for line in open(os.path.join(pdir, f)):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        try:
+            if (kv.get("kernel_source_sha") == sha and int(kv.get("n", -1)) == n
+                    and int(kv.get("layers", -1)) == layers and kv.get("precision") == precision):
+                return int(kv["dram_bytes_per_launch"])
+        except (KeyError, ValueError):
+            continue
+    return None
+
+
 def eff_tflops(layers, n, ms):
     return layers * 2.0 * float(n) ** 3 / (ms * 1e-3) / 1e12
 
@@ -229,15 +269,16 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms_local = ev0.elapsed_time(ev1) / args.steps
     res = results[-1]
     L = res.layers
     launches_per_step = 5  # Gershgorin, input layer, persistent layer kernel, output copy, final reduction
-    value = world * eff_tflops(L, n, ms)
+    # Replicas: every rank solves its own copy; the whole-job rate is the work of
+    # all ranks over the slowest rank's step time.
+    from paper_2107_02737_gb300 import shard
+
+    ms, work = shard.aggregate_step_time(ms_local, L * 2.0 * float(n) ** 3, device=dev)
+    value = work / (ms * 1e-3) / 1e12
 
     # ---- accuracy of the timed result (device-side checks) ----
     Dd = D.double()
@@ -283,14 +324,14 @@ def main():
         "config": {"workload": f"water-like banded tight-binding H, N={n}, n_occ={n_occ}, gap>=0.05 (seeded)",
                    "n": n, "n_occ": n_occ, "precision": f"split {args.precision} hi/lo, FP32 accumulation",
                    "l2": "inputs larger than L2 (H is 537 MB FP64; split operands 402 MB)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single", "kernel_sha": kernel_source_sha()},
         "layers": L, "stop_reason": res.stop_reason, "cta_group": res.cta_group,
         "accuracy": {"fro_err_vs_fp64_per_sqrtN": None, "idempotency_fro": idem, "trace_err": res.trace_D - n_occ,
                      "commutator_fro": comm, "band_energy": res.band_energy},
         "fp32_simt": {"ms_per_step": ms32, "value": eff_tflops(r32.layers, n, ms32), "unit": "TFLOP/s",
                       "layers": r32.layers, "trace_err": r32.trace_D - n_occ, "speedup_split_vs_fp32": ms32 / ms},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
-                     "frac": achieved / peak_sus, "traffic": None,
+                     "frac": achieved / peak_sus, "traffic": profiled_traffic(n, L, args.precision),
                      "kernel": "k_tc_persistent (all layers, one launch)", "kernel_ms": k_ms,
                      "algorithmic": f"{L} layers x 2N^3 flops",
                      "peak_kind": f"{peak_kind} cuBLAS bf16 sustained (burst {peak_burst})"},

@@ -119,7 +119,11 @@ typedef struct {
     double eps_max;
     int profile;          /* 1 = record per-phase device times into sp2_stats.phase_ms */
     int cta_group;        /* tensor-core tiles: 0 = choose (default), 1 = one CTA per 128 x 256
-                             tile, 2 = a CTA pair per 256 x 256 tile (M = 256 MMAs) */
+                             tile (cooperative launch), 2 = a CTA pair per 256 x 256 tile
+                             (M = 256 MMAs; a cluster launch sized to the pairs the device
+                             holds at once: work running concurrently on the same GPU can
+                             deny that residency, and the call then ends with
+                             SP2_ERR_TIMEOUT after timeout_ms) */
 } sp2_opts;
 
 /* Fill `o` with the defaults. */

@@ -698,20 +698,24 @@ cudaError_t launch_tc_persistent(const RunParams &p, int cta_group, int grid, cu
     if (cta_group == 1)
         return cudaLaunchCooperativeKernel(tc_kernel_ptr<1>(p.precision), dim3(grid), dim3(TC_THREADS), args,
                                            SMEM_BYTES, s);
+    // CTA pairs: a cluster launch of exactly as many pairs as the device holds
+    // at once (cudaOccupancyMaxActiveClusters, one CTA per SM), so on an idle GPU
+    // every pair is resident for the grid barrier.  Without the cooperative
+    // attribute (which the profiler cannot replay together with clusters) that
+    // residency is not promised by the API: if concurrent work delays a pair,
+    // the barrier's time limit ends the call with SP2_ERR_TIMEOUT.
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeCooperative;
-    attr[1].val.cooperative = 1;
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(TC_THREADS);
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = s;
     cfg.attrs = attr;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelExC(&cfg, tc_kernel_ptr<2>(p.precision), args);
 }
 

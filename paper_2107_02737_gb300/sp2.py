@@ -225,14 +225,14 @@ def density(H: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp
 
 def response(H: torch.Tensor, H1: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16",
              max_layers: int = 100, timeout_ms: float = 2000.0, fwd: Optional[Result] = None,
-             workspace: Optional[torch.Tensor] = None, stream=None):
+             workspace: Optional[torch.Tensor] = None, stream=None, bounds=None, cta_group: int = 0):
     """First-order response of the chain; returns (D, D1, Result)."""
     H, H1 = _f64(H, "H"), _f64(H1, "H1")
     n = _square(H, "H")
     D = torch.empty((n, n), dtype=torch.float32, device=H.device)
     D1 = torch.empty((n, n), dtype=torch.float32, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms)
+    o = make_opts(precision, max_layers, timeout_ms, bounds, cta_group=cta_group)
     ws, wsb = _ws_args(workspace)
     fp = ctypes.byref(fwd.raw) if fwd is not None else None
     s = load().sp2_response(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(H1.data_ptr()), n, float(n_occ),
