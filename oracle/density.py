@@ -115,3 +115,32 @@ def response_from_eigensystem(lam, C, H1, n_occ) -> np.ndarray:
 def adjoint(H: np.ndarray, G: np.ndarray, n_occ: int) -> np.ndarray:
     """Gradient of Tr[D(H) G] with respect to symmetric H (self-adjoint response)."""
     return response(H, symmetrise(G), n_occ)
+
+
+# -- non-orthogonal basis (section "The density matrix": H_orth = Z^T H Z, D = Z D_orth Z^T) --
+
+def density_matrix_generalized(H: np.ndarray, S: np.ndarray, n_occ: int) -> np.ndarray:
+    """D = sum_k f_k c_k c_k^T for H c = eps S c with C^T S C = I (Eq. KS-matrix, Eq. DM-outer-product)."""
+    import scipy.linalg
+
+    lam, C = scipy.linalg.eigh(np.asarray(H, np.float64), np.asarray(S, np.float64))
+    return density_from_eigensystem(C, n_occ)
+
+
+def inverse_factor_lowdin(S: np.ndarray) -> np.ndarray:
+    """Z = S^(-1/2), one inverse factor with Z^T S Z = I."""
+    lam, U = np.linalg.eigh(np.asarray(S, np.float64))
+    return (U / np.sqrt(lam)) @ U.T
+
+
+def inverse_factor_cholesky(S: np.ndarray) -> np.ndarray:
+    """Z = L^(-T) from S = L L^T, another inverse factor with Z^T S Z = I."""
+    L = np.linalg.cholesky(np.asarray(S, np.float64))
+    return np.linalg.inv(L).T
+
+
+def density_matrix_via_factor(H: np.ndarray, Z: np.ndarray, n_occ: int) -> np.ndarray:
+    """D = Z theta(mu I - Z^T H Z) Z^T (the orthogonalised route of section "The density matrix")."""
+    Z = np.asarray(Z, np.float64)
+    Hp = Z.T @ np.asarray(H, np.float64) @ Z
+    return Z @ density_matrix(symmetrise(Hp), n_occ) @ Z.T

@@ -279,5 +279,22 @@ def chain_derivative_eigenbasis(H: np.ndarray, H1: np.ndarray, choices: Sequence
     return C @ (h1 * phi) @ C.T
 
 
+def refine(X: np.ndarray, n_occ: float, layers: int = 2):
+    """Refinement: `layers` further layers of the same network in float64.
+
+    The paper adds a few final layers in which X is held in double precision so
+    that the eigenvalues are purified closer to 0 and 1 (section "Deep-neural
+    network electronic structure solver", the refinement step).  Each layer
+    takes its sign by the same trace-correcting rule.  Returns (X, stats).
+    """
+    X = np.asarray(X, np.float64)
+    stats = [_stat(X, INPUT)]
+    for _ in range(layers):
+        c = layer_choice(stats[-1].trace, stats[-1].trace_sq, n_occ)
+        X = apply_layer(X, c)
+        stats.append(_stat(X, c))
+    return X, stats
+
+
 def band_energy_of(D: np.ndarray, H: np.ndarray) -> float:
     return float(np.sum(np.asarray(D, np.float64) * np.asarray(H, np.float64)))

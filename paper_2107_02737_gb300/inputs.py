@@ -122,6 +122,22 @@ def banded_perturbation(n: int, rng: np.random.Generator, bandwidth: int = 64,
     return h
 
 
+def overlap_matrix(n: int, rng: np.random.Generator, bandwidth: int = 16, sigma: float = 0.05,
+                   decay: float = 4.0) -> np.ndarray:
+    """Symmetric positive-definite overlap S = I + banded off-diagonal terms.
+
+    Off-diagonal entries N(0, sigma^2) exp(-|i-j|/decay) within the band; the
+    band is scaled down if needed so that its row sums stay below 1/2, which
+    keeps the eigenvalues of S inside [1/2, 3/2] (Gershgorin).
+    """
+    b = banded_matrix(n, rng, bandwidth=bandwidth, offdiag_sigma=sigma, decay=decay, onsite_sigma=0.0)
+    np.fill_diagonal(b, 0.0)
+    rmax = np.abs(b).sum(axis=1).max()
+    if rmax > 0.5:
+        b *= 0.5 / rmax
+    return np.eye(n) + b
+
+
 def symmetric_gaussian(n: int, rng: np.random.Generator) -> np.ndarray:
     a = rng.standard_normal((n, n))
     return 0.5 * (a + a.T)

@@ -155,3 +155,45 @@ def test_no_gap_is_rejected():
     H = np.diag([0.0, 1.0, 1.0, 2.0])
     with pytest.raises(ValueError):
         density.response(H, np.eye(4), 2)
+
+
+# -- non-orthogonal basis ------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def nonorth():
+    rng = np.random.default_rng(31)
+    n = 60
+    H = inputs.symmetric_gaussian(n, rng) * 0.3
+    S = inputs.overlap_matrix(n, rng)
+    return H, S, 23
+
+
+def test_overlap_is_positive_definite(nonorth):
+    _, S, _ = nonorth
+    lam = np.linalg.eigvalsh(S)
+    assert 0.5 <= lam[0] and lam[-1] <= 1.5
+
+
+def test_inverse_factors(nonorth):
+    _, S, _ = nonorth
+    for Z in (density.inverse_factor_lowdin(S), density.inverse_factor_cholesky(S)):
+        np.testing.assert_allclose(Z.T @ S @ Z, np.eye(S.shape[0]), atol=1e-12)
+
+
+def test_orthogonalised_route_matches_generalised_eigenproblem(nonorth):
+    H, S, n_occ = nonorth
+    ref = density.density_matrix_generalized(H, S, n_occ)
+    for Z in (density.inverse_factor_lowdin(S), density.inverse_factor_cholesky(S)):
+        # D does not depend on which inverse factor is used
+        np.testing.assert_allclose(density.density_matrix_via_factor(H, Z, n_occ), ref, atol=1e-11)
+    # idempotency in the S metric, occupation, and [H, D] in the S metric
+    np.testing.assert_allclose(ref @ S @ ref, ref, atol=1e-11)
+    assert np.trace(ref @ S) == pytest.approx(n_occ, abs=1e-10)
+    np.testing.assert_allclose(H @ ref @ S, S @ ref @ H, atol=1e-11)
+
+
+def test_identity_overlap_reduces_to_orthogonal(nonorth):
+    H, _, n_occ = nonorth
+    n = H.shape[0]
+    np.testing.assert_allclose(density.density_matrix_generalized(H, np.eye(n), n_occ),
+                               density.density_matrix(H, n_occ), atol=1e-12)

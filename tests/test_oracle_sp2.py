@@ -175,3 +175,32 @@ def test_chain_adjoint_asymmetric_weight(diff_case):
     a = sp2.chain_adjoint(ham.H, G, r.choices, r.eps_min, r.eps_max)
     b = sp2.chain_adjoint(ham.H, 0.5 * (G + G.T), r.choices, r.eps_min, r.eps_max)
     np.testing.assert_allclose(a, b, atol=1e-14)
+
+
+def test_refinement_purifies_quadratically():
+    # A projector with eigenvalues nudged by delta: two refinement layers map
+    # 1 + d -> 1 - O(d^2) and d -> O(d^2) (closed form on a diagonal matrix).
+    d = np.array([1e-4, -2e-4, 3e-4, -1e-4])
+    lam = np.array([1.0, 1.0, 0.0, 0.0]) + d
+    X, stats = sp2.refine(np.diag(lam), 2, layers=2)
+    # by hand: Tr X = 2 + 1e-4 > 2 and the rule picks X^2 first, then 2X - X^2,
+    # so every eigenvalue becomes 2 lam^2 - lam^4
+    assert [s.choice for s in stats[1:]] == [sp2.SQUARE, sp2.FLIP]
+    np.testing.assert_allclose(np.diag(X), 2 * lam ** 2 - lam ** 4, rtol=0, atol=1e-15)
+    dev = np.minimum(np.abs(np.diag(X)), np.abs(1 - np.diag(X)))
+    assert np.max(dev) < 2.5 * np.max(np.abs(d)) ** 2
+    assert abs(stats[-1].idem) < 2 * np.sum(np.abs(d)) ** 2
+    # the chosen signs follow the trace rule layer by layer
+    for k in range(1, len(stats)):
+        assert stats[k].choice == sp2.layer_choice(stats[k - 1].trace, stats[k - 1].trace_sq, 2)
+
+
+def test_refinement_of_perturbed_density(c0_small):
+    # An FP32-rounded converged chain refined in float64 reaches float64 idempotency.
+    r = sp2.sp2(c0_small.H, c0_small.n_occ)
+    X32 = r.D.astype(np.float32).astype(np.float64)
+    X, stats = sp2.refine(X32, c0_small.n_occ, layers=2)
+    assert np.linalg.norm(X @ X - X) < 1e-9
+    assert abs(np.trace(X) - c0_small.n_occ) < 1e-9
+    D = density.density_matrix(c0_small.H, c0_small.n_occ)
+    assert np.linalg.norm(X - D) / np.sqrt(c0_small.n) < 1e-6
