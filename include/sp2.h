@@ -216,6 +216,35 @@ sp2_status sp2_apply_layers(const float *X0, int N, const int *choices, int n_la
                             sp2_stats *st, const sp2_opts *o, void *stream);
 
 /*
+ * sp2_density_refined -- the chain of sp2_density followed by `refine_layers`
+ * further layers with X held in FP64 (section "Deep-neural network electronic
+ * structure solver": extra layers with a double-precision representation of X
+ * act as a refinement that purifies the eigenvalues closer to 1 and 0).  Each
+ * refinement layer takes its sign by the same trace rule, decided on the device;
+ * the square is an FP64 GEMM emulated on the tensor cores (cuBLAS).
+ *   refine_layers [in]  0 .. 8 (the paper uses two).
+ *   D             [out] N x N FP64, the refined density matrix.
+ *   st            [out] the chain's layers followed by the refinement layers;
+ *                       trace_D and band_energy from the FP64 result.
+ * Allocates device memory for the FP64 matrices (3 N^2 doubles + the chain's
+ * workspace) and frees it before returning.
+ */
+sp2_status sp2_density_refined(const double *H, int N, double n_occ, double tol, int refine_layers, double *D,
+                               sp2_stats *st, const sp2_opts *o, void *stream);
+
+/*
+ * sp2_density_nonorth -- density matrix in a non-orthogonal basis (section "The
+ * density matrix"): with Z an inverse factor of the overlap S (Z^T S Z = I),
+ * H_orth = Z^T H Z, D_orth = theta(mu I - H_orth) by the chain (plus
+ * `refine_layers` FP64 layers), and D = Z D_orth Z^T.  The congruences are FP64
+ * GEMMs emulated on the tensor cores.  D does not depend on which Z is given.
+ *   Z [in]  N x N FP64, row-major.
+ *   D [out] N x N FP64; band_energy = Tr[D H].
+ */
+sp2_status sp2_density_nonorth(const double *H, const double *Z, int N, double n_occ, double tol,
+                               int refine_layers, double *D, sp2_stats *st, const sp2_opts *o, void *stream);
+
+/*
  * sp2_density_noalloc -- sp2_density without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory once running, such as an MD engine whose memory

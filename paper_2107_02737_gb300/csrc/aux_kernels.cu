@@ -65,7 +65,8 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
     return r;
 }
 
-// Gershgorin discs: one warp per row, FP64 row sums of |H_ij|, j != i.
+// Gershgorin discs: one warp per row, FP64 row sums of |H_ij|, j != i.  Each
+// lane keeps eight loads in flight and four partial sums (fixed order).
 __global__ void __launch_bounds__(AUX_THREADS) k_gershgorin(InstDesc *inst) {
     const InstDesc &d = inst[blockIdx.y];
     const int n = d.n;
@@ -73,25 +74,27 @@ __global__ void __launch_bounds__(AUX_THREADS) k_gershgorin(InstDesc *inst) {
     double lo = INFINITY, hi = -INFINITY;
     int bad = 0;
     for (int row = blockIdx.x * (AUX_THREADS / 32) + w; row < n; row += gridDim.x * (AUX_THREADS / 32)) {
-        const double *h = d.H + (size_t)row * n;
-        double r0 = 0.0, r1 = 0.0;
-        int j = lane;
-        for (; j + 32 < n; j += 64) {
-            double v0 = h[j], v1 = h[j + 32];
-            bad |= !isfinite(v0) | !isfinite(v1);
-            r0 += (j == row) ? 0.0 : fabs(v0);
-            r1 += (j + 32 == row) ? 0.0 : fabs(v1);
+        const double *__restrict__ h = d.H + (size_t)row * n;
+        double r[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int j0 = lane; j0 < n; j0 += 32 * 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + 32 * u;
+                v[u] = (j < n) ? h[j] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + 32 * u;
+                bad |= !isfinite(v[u]);
+                r[u & 3] += (j != row) ? fabs(v[u]) : 0.0;
+            }
         }
-        if (j < n) {
-            double v0 = h[j];
-            bad |= !isfinite(v0);
-            r0 += (j == row) ? 0.0 : fabs(v0);
-        }
-        double r = warp_sum_d(r0 + r1);
-        r = __shfl_sync(0xffffffffu, r, 0);
+        double rs = warp_sum_d((r[0] + r[1]) + (r[2] + r[3]));
+        rs = __shfl_sync(0xffffffffu, rs, 0);
         const double dv = h[row];
-        lo = fmin(lo, dv - r);
-        hi = fmax(hi, dv + r);
+        lo = fmin(lo, dv - rs);
+        hi = fmax(hi, dv + rs);
     }
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
@@ -142,13 +145,17 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
     const double delta = emax - emin;
     const bool degenerate = !(delta > 0.0) || !isfinite(delta) || d.ctl->nonfinite;
     const double inv = degenerate ? 0.0 : 1.0 / delta;
-    float *xf = d.xf[0];
-    uint16_t *op0 = d.xop, *op1 = d.xop + (size_t)np * np, *op2 = d.xop + 2 * (size_t)np * np;
+    float *__restrict__ xf = d.xf[0];
+    uint16_t *__restrict__ op0 = d.xop;
+    uint16_t *__restrict__ op1 = d.xop + (size_t)np * np;
+    uint16_t *__restrict__ op2 = d.xop + 2 * (size_t)np * np;
     FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
     // Rows are strided over blocks, four consecutive columns per thread: no
-    // index divisions on the hot loop.
+    // index divisions on the hot loop; restrict-qualified so that the loads of
+    // the next columns can be issued ahead of this group's stores.
     for (int i = blockIdx.x; i < np; i += gridDim.x) {
-        const double *hrow = d.H + (size_t)i * n;
+        const double *__restrict__ hrow = d.H + (size_t)(i < n ? i : 0) * n;
+#pragma unroll 2
         for (int j0 = threadIdx.x * 4; j0 < np; j0 += AUX_THREADS * 4) {
             const size_t idx = (size_t)i * np + j0;
             float x[4], y[4];
@@ -265,45 +272,58 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode
     if (blockIdx.x == 0 && threadIdx.x == 0) d.ctl->y_scale = yscale;
 }
 
-// D = X_L (un-padded copy), partial FP64 sums of D_ij H_ij and D_ii per block;
-// the response / adjoint output is the Y stream with its scale removed.
+// D = X_L (un-padded copy, diagonal offset added), FP64 partials of Tr[D H] and
+// Tr D per block; the response / adjoint output is the Y stream with its scale
+// removed.  X is stored exactly symmetric and H is symmetric, so Tr[D H] is
+// summed over the upper triangle with off-diagonal weight 2 (half the FP64 work).
 __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mode) {
     const InstDesc &d = inst[blockIdx.y];
     if (blockIdx.x >= d.fin_blocks) return;
     const int n = d.n, np = d.np;
     const InstCtl *ctl = d.ctl;
-    const float *X = d.xf[ctl->final_x & 1];
-    const float *Y = d.yf[ctl->final_y & 1];
+    const float *__restrict__ X = d.xf[ctl->final_x & 1];
+    const float *__restrict__ Y = d.yf[ctl->final_y & 1];
+    const double *__restrict__ H = d.H;
+    float *__restrict__ out = d.out;
+    float *__restrict__ out1 = d.out1;
     const float xoff = (float)ctl->x_offset;
+    const bool second = (mode == MODE_RESPONSE || mode == MODE_ADJOINT);
     float ys = 0.0f;
     if (mode == MODE_RESPONSE) ys = (float)(1.0 / ctl->y_scale);
     if (mode == MODE_ADJOINT) ys = (float)(-1.0 / (ctl->y_scale * (ctl->eps_max - ctl->eps_min)));
     double e = 0.0, tr = 0.0;
     for (int i = blockIdx.x; i < n; i += d.fin_blocks) {
+        const float *__restrict__ xrow = X + (size_t)i * np;
+        const size_t base = (size_t)i * n;
+#pragma unroll 4
         for (int j = threadIdx.x; j < n; j += AUX_THREADS) {
-            const size_t idx = (size_t)i * n + j;
-            float x = X[(size_t)i * np + j];
-            if (i == j) x += xoff;  // true X_L = stored X_L + c_L I
-            if (d.out) d.out[idx] = x;
-            if (d.H) e += (double)x * d.H[idx];
-            if (i == j) tr += x;
-            if (mode == MODE_RESPONSE || mode == MODE_ADJOINT) d.out1[idx] = Y[(size_t)i * np + j] * ys;
+            float x = xrow[j];
+            if (i == j) {
+                x += xoff;  // true X_L = stored X_L + c_L I
+                tr += x;
+            }
+            if (out) out[base + j] = x;
+            if (H && j >= i) e += (j == i ? 1.0 : 2.0) * (double)x * H[base + j];
+            if (second) out1[base + j] = Y[(size_t)i * np + j] * ys;
         }
     }
     double2 s = block_sum2(e, tr);
     if (threadIdx.x == 0) d.fin_part[blockIdx.x] = s;
 }
 
-__global__ void k_finalize_reduce(InstDesc *inst) {
+// One block per instance: fixed-stride partial sums, then the fixed block tree.
+__global__ void __launch_bounds__(AUX_THREADS) k_finalize_reduce(InstDesc *inst) {
     const InstDesc &d = inst[blockIdx.x];
-    if (threadIdx.x != 0) return;
     double e = 0.0, tr = 0.0;
-    for (int k = 0; k < d.fin_blocks; ++k) {
+    for (int k = threadIdx.x; k < d.fin_blocks; k += AUX_THREADS) {
         e += d.fin_part[k].x;
         tr += d.fin_part[k].y;
     }
-    d.ctl->band_energy = e;
-    d.ctl->trace_D = tr;
+    double2 s = block_sum2(e, tr);
+    if (threadIdx.x == 0) {
+        d.ctl->band_energy = s.x;
+        d.ctl->trace_D = s.y;
+    }
 }
 
 __global__ void k_fill_trivial(float *D, int n, float diag) {
@@ -372,7 +392,7 @@ cudaError_t launch_finalize(InstDesc *inst, int B, int max_n, int mode, cudaStre
     k_finalize<<<grid, AUX_THREADS, 0, s>>>(inst, mode);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_finalize_reduce<<<B, 32, 0, s>>>(inst);
+    k_finalize_reduce<<<B, AUX_THREADS, 0, s>>>(inst);
     return cudaGetLastError();
 }
 

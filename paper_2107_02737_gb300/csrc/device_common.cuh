@@ -160,7 +160,7 @@ struct RoundCtl {
     double chist_c[MAX_L + 2];       // adjoint (B = 1): c_n per layer
 };
 
-__device__ __forceinline__ int layer_rule(double t, double q, double n_occ) {
+__host__ __device__ __forceinline__ int layer_rule(double t, double q, double n_occ) {
     return fabs(q - n_occ) <= fabs(2.0 * t - q - n_occ) ? SP2_CHOICE_SQUARE : SP2_CHOICE_FLIP;
 }
 

@@ -1,0 +1,112 @@
+"""Timing of the secondary workloads (one JSON line each).
+
+    python -m paper_2107_02737_gb300.measure --workload batched|response|adjoint|md
+
+* ``batched``  — 64 gapped Hamiltonians of N in {128, ..., 2048}, BF16 split, one
+  grouped persistent launch per step; effective TFLOP/s = sum_i L_i 2 N_i^3 / t.
+* ``response`` — D and D1 at N = 4096 (water-like H, banded H1); counts 4 N^3 per
+  layer (the square and the product X X1).
+* ``adjoint``  — dTr[DG]/dH at N = 4096, forward replayed from a density run;
+  counts 2 N^3 (forward) + 2 N^3 (reverse) per layer.
+* ``md``       — H_k = H_0 + sin(0.05 k) V through sp2_response (see md.py).
+* ``refined``  — the N = 8192 chain plus two FP64 refinement layers (cuBLAS FP64
+  emulated on the tensor cores); reports the added time and the trace.
+
+Device time with CUDA events around each call, after warm-up; inputs resident on
+the device.  These are reports, not the headline benchmark (bench.py).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import inputs, md
+from . import sp2
+
+
+def _time(fn, steps, warmup):
+    for _ in range(warmup):
+        out = fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def batched(steps, warmup, precision="bf16"):
+    hams = inputs.batched_workload(64)
+    Hs = [torch.tensor(h.H, device="cuda") for h in hams]
+    occ = [h.n_occ for h in hams]
+    ms, (Ds, res, status) = _time(lambda: sp2.density_batched(Hs, occ, precision=precision), steps, warmup)
+    work = sum(r.layers * 2.0 * h.n ** 3 for r, h in zip(res, hams))
+    # Accuracy by properties that hold for the exact D: idempotency and trace.
+    idem = max(float(torch.linalg.norm(D.double() @ D.double() - D.double())) / np.sqrt(h.n)
+               for h, D in zip(hams, Ds))
+    tr = max(abs(r.trace_D - h.n_occ) for h, r in zip(hams, res))
+    seq_ms = 0.0
+    for h, H in zip(hams, Hs):
+        t, _ = _time(lambda: sp2.density(H, h.n_occ, precision=precision), 1, 1)
+        seq_ms += t
+    return {"workload": "batched 64 x N in {128..2048}", "precision": precision, "ms_per_step": ms,
+            "effective_tflops": work / (ms * 1e-3) / 1e12, "sum_layers": sum(r.layers for r in res),
+            "one_by_one_ms": seq_ms, "max_idempotency_per_sqrtN": idem, "max_trace_err": tr, "status": status}
+
+
+def response(steps, warmup, n=4096):
+    ham, H1, _ = inputs.differentiation_workload(n)
+    H, H1d = torch.tensor(ham.H, device="cuda"), torch.tensor(H1, device="cuda")
+    ms, (D, D1, res) = _time(lambda: sp2.response(H, H1d, ham.n_occ), steps, warmup)
+    return {"workload": f"response N={n}", "ms_per_step": ms, "layers": res.layers, "d1_norm": float(D1.norm()),
+            "effective_tflops": res.layers * 4.0 * n ** 3 / (ms * 1e-3) / 1e12}
+
+
+def adjoint(steps, warmup, n=4096):
+    ham, _, G = inputs.differentiation_workload(n)
+    H, Gd = torch.tensor(ham.H, device="cuda"), torch.tensor(G, device="cuda")
+    _, fwd = sp2.density(H, ham.n_occ)
+    ms, (D, dH, res) = _time(lambda: sp2.adjoint(H, Gd, ham.n_occ, fwd=fwd), steps, warmup)
+    return {"workload": f"adjoint N={n}", "ms_per_step": ms, "layers": res.layers,
+            "effective_tflops": res.layers * 4.0 * n ** 3 / (ms * 1e-3) / 1e12,
+            "workspace_gb": sp2.workspace_bytes(n, "adjoint", layers=res.layers) / 1e9}
+
+
+def refined(steps, warmup, n=8192, layers=2):
+    ham = inputs.water_like_workload(n)
+    H = torch.tensor(ham.H, device="cuda")
+    ms_chain, (_, r0) = _time(lambda: sp2.density(H, ham.n_occ), steps, warmup)
+    ms, (D, res) = _time(lambda: sp2.density_refined(H, ham.n_occ, refine_layers=layers), steps, warmup)
+    return {"workload": f"refined N={n}", "refine_layers": layers, "ms_per_step": ms, "chain_ms": ms_chain,
+            "refinement_ms": ms - ms_chain, "trace_err": res.trace_D - ham.n_occ,
+            "chain_trace_err": r0.trace_D - ham.n_occ, "idem_fro": float(torch.linalg.norm(D @ D - D))}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", choices=["batched", "response", "adjoint", "md", "refined"], required=True)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--n", type=int, default=0)
+    a = ap.parse_args(argv)
+    if a.workload == "batched":
+        out = batched(a.steps, a.warmup)
+    elif a.workload == "response":
+        out = response(a.steps, a.warmup, a.n or 4096)
+    elif a.workload == "adjoint":
+        out = adjoint(a.steps, a.warmup, a.n or 4096)
+    elif a.workload == "refined":
+        out = refined(a.steps, a.warmup, a.n or 8192)
+    else:
+        return md.main(["--n", str(a.n or 12288), "--steps", str(a.steps)])
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

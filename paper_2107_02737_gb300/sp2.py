@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
 EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
            "sp2_response", "sp2_response_workspace_bytes", "sp2_adjoint", "sp2_adjoint_workspace_bytes",
            "sp2_density_batched", "sp2_density_batched_workspace_bytes", "sp2_apply_layers",
-           "sp2_density_noalloc"]
+           "sp2_density_noalloc", "sp2_density_refined", "sp2_density_nonorth"]
 NOALLOC_MAX_N = 512
 
 _lib = None
@@ -96,6 +96,10 @@ def load() -> ctypes.CDLL:
     lib.sp2_apply_layers.restype = c_i
     lib.sp2_density_noalloc.argtypes = [c_p, c_i, c_d, c_d, c_p, P(Stats), P(Opts), c_p]
     lib.sp2_density_noalloc.restype = c_i
+    lib.sp2_density_refined.argtypes = [c_p, c_i, c_d, c_d, c_i, c_p, P(Stats), P(Opts), c_p]
+    lib.sp2_density_refined.restype = c_i
+    lib.sp2_density_nonorth.argtypes = [c_p, c_p, c_i, c_d, c_d, c_i, c_p, P(Stats), P(Opts), c_p]
+    lib.sp2_density_nonorth.restype = c_i
     _lib = lib
     return lib
 
@@ -328,6 +332,36 @@ def density_noalloc(H: torch.Tensor, n_occ: int, out: torch.Tensor, tol: float =
                                    ctypes.c_void_p(_stream_handle(H, stream)))
     _check(s, "sp2_density_noalloc")
     return out, _result(s, st)
+
+
+def density_refined(H: torch.Tensor, n_occ: int, refine_layers: int = 2, tol: float = 1e-6,
+                    precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0, stream=None):
+    """The chain plus ``refine_layers`` FP64 layers; returns (D float64, Result)."""
+    H = _f64(H, "H")
+    n = _square(H, "H")
+    D = torch.empty((n, n), dtype=torch.float64, device=H.device)
+    st = _new_stats()
+    o = make_opts(precision, max_layers, timeout_ms)
+    s = load().sp2_density_refined(ctypes.c_void_p(H.data_ptr()), n, float(n_occ), float(tol), int(refine_layers),
+                                   ctypes.c_void_p(D.data_ptr()), ctypes.byref(st), ctypes.byref(o),
+                                   ctypes.c_void_p(_stream_handle(H, stream)))
+    _check(s, "sp2_density_refined")
+    return D, _result(s, st)
+
+
+def density_nonorth(H: torch.Tensor, Z: torch.Tensor, n_occ: int, refine_layers: int = 0, tol: float = 1e-6,
+                    precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0, stream=None):
+    """D = Z theta(mu I - Z^T H Z) Z^T (float64) for an inverse overlap factor Z; returns (D, Result)."""
+    H, Z = _f64(H, "H"), _f64(Z, "Z")
+    n = _square(H, "H")
+    D = torch.empty((n, n), dtype=torch.float64, device=H.device)
+    st = _new_stats()
+    o = make_opts(precision, max_layers, timeout_ms)
+    s = load().sp2_density_nonorth(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(Z.data_ptr()), n, float(n_occ),
+                                   float(tol), int(refine_layers), ctypes.c_void_p(D.data_ptr()), ctypes.byref(st),
+                                   ctypes.byref(o), ctypes.c_void_p(_stream_handle(H, stream)))
+    _check(s, "sp2_density_nonorth")
+    return D, _result(s, st)
 
 
 def device_info():
