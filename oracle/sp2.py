@@ -33,6 +33,24 @@ here (and identically by the CUDA path):
 Layer statistics follow the CUDA path's record: entry n holds Tr X_n,
 ||X_n||_F^2, Tr X_n - ||X_n||_F^2 and the choice that produced X_n (-1 for the
 input layer, 0 for X^2, 1 for 2X - X^2).
+
+Accelerated chain.  Section "GPU and tensor core performance" remarks that up
+to half of the layers can be saved when estimates of the highest occupied and
+lowest unoccupied eigenvalues are known, and leaves that scheme out.  The
+reading used here (and by the CUDA path): with the images x_lumo < x_homo of
+an estimated interval [eps_homo, eps_lumo] under the input layer, every layer
+first expands X affinely and then applies its branch,
+
+    X^2 branch:     T_n = a_n X_n + (1 - a_n) I,  a_n = 2 / (2 - x_lumo),  X_{n+1} = T_n^2
+    2X - X^2 branch: T_n = a_n X_n,               a_n = 2 / (1 + x_homo),  X_{n+1} = 2 T_n - T_n^2
+
+(a layer S_n = W_n X_n + B_n of the same network with scalar weights), and
+x_lumo, x_homo follow the same scalar map.  The branch is still taken by the
+trace rule.  a_n lies in [1, 2], so every image stays in [0, 1]; a_n = 1 (the
+interval [eps_min, eps_max]) is the plain chain.  The occupied images stay
+above the unoccupied ones after every layer, so the chain still converges to
+theta(mu I - H), whenever the estimated interval overlaps the gap:
+eps_lumo > eps_HOMO and eps_homo < eps_LUMO.
 """
 from __future__ import annotations
 
@@ -71,6 +89,7 @@ class SP2Result:
     converged: bool
     eps_min: float
     eps_max: float
+    alphas: List[float] = dataclasses.field(default_factory=list)  # a_n per layer (1 = plain)
 
     @property
     def layers(self) -> int:
@@ -121,9 +140,44 @@ def stop_check(idem: Sequence[float], tol: float, max_layers: int) -> int:
     return 0
 
 
-def apply_layer(X: np.ndarray, choice: int) -> np.ndarray:
-    S = X @ X
-    return S if choice == SQUARE else 2.0 * X - S
+def apply_layer(X: np.ndarray, choice: int, alpha: float = 1.0) -> np.ndarray:
+    """X_{n+1} from X_n: T = a X + (1 - a) I then T^2, or T = a X then 2T - T^2."""
+    if alpha == 1.0:  # the plain layer: X^2 or 2X - X^2
+        S = X @ X
+        return S if choice == SQUARE else 2.0 * X - S
+    if choice == SQUARE:
+        T = alpha * X + (1.0 - alpha) * np.eye(X.shape[0])
+        return T @ T
+    T = alpha * X
+    return 2.0 * T - T @ T
+
+
+def gap_images(gap, eps_min: float, eps_max: float):
+    """(x_lumo, x_homo): images of an estimated interval (eps_homo, eps_lumo) under the
+    input layer, clipped to [0, 1]; (0, 1), the plain chain, when there is no estimate."""
+    if gap is None:
+        return 0.0, 1.0
+    eps_homo, eps_lumo = gap
+    if not eps_homo < eps_lumo:
+        raise ValueError("the estimated interval needs eps_homo < eps_lumo")
+    span = eps_max - eps_min
+    x_lumo = min(max((eps_max - eps_lumo) / span, 0.0), 1.0)
+    x_homo = min(max((eps_max - eps_homo) / span, 0.0), 1.0)
+    return x_lumo, x_homo
+
+
+def expansion(choice: int, x_lumo: float, x_homo: float) -> float:
+    """a_n of the accelerated layer: 2/(2 - x_lumo) before X^2, 2/(1 + x_homo) before 2X - X^2."""
+    return 2.0 / (2.0 - x_lumo) if choice == SQUARE else 2.0 / (1.0 + x_homo)
+
+
+def scalar_layer(x, choice: int, alpha: float = 1.0):
+    """The same layer on scalars (eigenvalues or the tracked interval ends)."""
+    if choice == SQUARE:
+        t = alpha * x + (1.0 - alpha)
+        return t * t
+    t = alpha * x
+    return 2.0 * t - t * t
 
 
 def _stat(X: np.ndarray, choice: int) -> LayerStat:
@@ -136,13 +190,15 @@ def _stat(X: np.ndarray, choice: int) -> LayerStat:
 
 def sp2(H: np.ndarray, n_occ: int, tol: float = DEFAULT_TOL,
         max_layers: int = DEFAULT_MAX_LAYERS, bounds=None,
-        choices: Optional[Sequence[int]] = None, keep_layers: bool = False) -> SP2Result:
+        choices: Optional[Sequence[int]] = None, keep_layers: bool = False,
+        gap=None) -> SP2Result:
     """Run the DNN-SP2 chain on H in float64.
 
     ``choices`` replays a given sign sequence exactly (used to follow a
     sequence taken by another implementation); the stop rule is then only
     evaluated for the report.  With ``keep_layers`` the result carries every X_n in
-    ``result.layers_X``.
+    ``result.layers_X``.  ``gap = (eps_homo, eps_lumo)`` runs the accelerated
+    chain (module docstring).
     """
     H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
@@ -153,27 +209,36 @@ def sp2(H: np.ndarray, n_occ: int, tol: float = DEFAULT_TOL,
         res.layers_X = [D]
         return res
     X = input_layer(H, eps_min, eps_max)
+    x_lumo, x_homo = gap_images(gap, eps_min, eps_max)
     stats = [_stat(X, INPUT)]
+    alphas = []
+    images = [(x_lumo, x_homo)]
     kept = [X] if keep_layers else None
+
+    def step(c):
+        nonlocal X, x_lumo, x_homo
+        a = expansion(c, x_lumo, x_homo)
+        X = apply_layer(X, c, a)
+        x_lumo, x_homo = scalar_layer(x_lumo, c, a), scalar_layer(x_homo, c, a)
+        alphas.append(a)
+        images.append((x_lumo, x_homo))
+        stats.append(_stat(X, c))
+        if keep_layers:
+            kept.append(X)
+
     if choices is not None:
         # Exact replay of a given sign sequence; the stop rule is only reported.
         for c in choices:
-            X = apply_layer(X, c)
-            stats.append(_stat(X, c))
-            if keep_layers:
-                kept.append(X)
+            step(c)
         reason = stop_check([s.idem for s in stats], tol, max_layers)
     else:
         reason = stop_check([stats[0].idem], tol, max_layers)
         while not reason:
-            c = layer_choice(stats[-1].trace, stats[-1].trace_sq, n_occ)
-            X = apply_layer(X, c)
-            stats.append(_stat(X, c))
-            if keep_layers:
-                kept.append(X)
+            step(layer_choice(stats[-1].trace, stats[-1].trace_sq, n_occ))
             reason = stop_check([s.idem for s in stats], tol, max_layers)
-    res = SP2Result(X, stats, reason, reason in (STOP_TOL, STOP_STALL), eps_min, eps_max)
+    res = SP2Result(X, stats, reason, reason in (STOP_TOL, STOP_STALL), eps_min, eps_max, alphas)
     res.layers_X = kept
+    res.gap_images = images  # (x_lumo, x_homo) after each layer, entry 0 for X_0
     return res
 
 
@@ -181,24 +246,27 @@ def sp2(H: np.ndarray, n_occ: int, tol: float = DEFAULT_TOL,
 
 def scalar_sp2(eigvals: np.ndarray, n_occ: int, eps_min: float, eps_max: float,
                tol: float = DEFAULT_TOL, max_layers: int = DEFAULT_MAX_LAYERS,
-               choices: Optional[Sequence[int]] = None):
+               choices: Optional[Sequence[int]] = None, gap=None):
     """The chain acting on the eigenvalues of H: x_0 = (eps_max - eps)/(eps_max - eps_min).
 
     Since every layer is a polynomial of X, X_n = C diag(p_n(eps)) C^T and
     Tr X_n = sum p_n, ||X_n||_F^2 = sum p_n^2.  Returns (p_L, stats, stop_reason,
     dp_L/dx) where the derivative is propagated by the scalar chain rule.
+    ``gap`` as for ``sp2``.
     """
     x = (eps_max - np.asarray(eigvals, np.float64)) / (eps_max - eps_min)
     dx = np.ones_like(x)
+    x_lumo, x_homo = gap_images(gap, eps_min, eps_max)
     stats = [LayerStat(float(x.sum()), float((x * x).sum()), float(x.sum() - (x * x).sum()), INPUT)]
     def step(c):
-        nonlocal x, dx
+        nonlocal x, dx, x_lumo, x_homo
+        a = expansion(c, x_lumo, x_homo)
         if c == SQUARE:
-            dx = 2.0 * x * dx
-            x = x * x
+            dx = 2.0 * a * (a * x + 1.0 - a) * dx
         else:
-            dx = (2.0 - 2.0 * x) * dx
-            x = 2.0 * x - x * x
+            dx = (2.0 * a - 2.0 * a * a * x) * dx
+        x = scalar_layer(x, c, a)
+        x_lumo, x_homo = scalar_layer(x_lumo, c, a), scalar_layer(x_homo, c, a)
         t, q = float(x.sum()), float((x * x).sum())
         stats.append(LayerStat(t, q, t - q, c))
 
@@ -217,49 +285,58 @@ def scalar_sp2(eigvals: np.ndarray, n_occ: int, eps_min: float, eps_max: float,
 # -- response, adjoint and derivative of the chain ----------------------------------
 
 def chain_response(H: np.ndarray, H1: np.ndarray, choices: Sequence[int],
-                   eps_min: float, eps_max: float) -> np.ndarray:
-    """Forward-mode derivative of the chain with the layer signs held fixed.
+                   eps_min: float, eps_max: float, alphas=None) -> np.ndarray:
+    """Forward-mode derivative of the chain with the layer signs (and a_n) held fixed.
 
-    X1_0 = -H1/(eps_max - eps_min); per layer, with C = X_n X1_n,
-    X1_{n+1} = C + C^T (for X^2) or 2 X1_n - (C + C^T) (for 2X - X^2),
-    alongside X_{n+1}.  Returns X1_L.
+    X1_0 = -H1/(eps_max - eps_min); per layer T = a X + (1 - a) I or a X and
+    T1 = a X1_n; with C = T T1, X1_{n+1} = C + C^T (for X^2) or 2 T1 - (C + C^T)
+    (for 2X - X^2), alongside X_{n+1}.  Returns X1_L.
     """
     X = input_layer(H, eps_min, eps_max)
     X1 = -np.asarray(H1, np.float64) / (eps_max - eps_min)
-    for c in choices:
-        P = X @ X1
+    n = X.shape[0]
+    for k, c in enumerate(choices):
+        a = 1.0 if alphas is None else alphas[k]
+        T = a * X + (1.0 - a) * np.eye(n) if c == SQUARE else a * X
+        T1 = a * X1
+        P = T @ T1
         P = P + P.T
-        S = X @ X
+        S = T @ T
         if c == SQUARE:
             X, X1 = S, P
         else:
-            X, X1 = 2.0 * X - S, 2.0 * X1 - P
+            X, X1 = 2.0 * T - S, 2.0 * T1 - P
     return X1
 
 
 def chain_adjoint(H: np.ndarray, G: np.ndarray, choices: Sequence[int],
-                  eps_min: float, eps_max: float) -> np.ndarray:
+                  eps_min: float, eps_max: float, alphas=None) -> np.ndarray:
     """Reverse-mode gradient of Tr[X_L G] with respect to symmetric H.
 
-    G_L = sym(G); for the layer that made X_{n+1} from X_n,
-    G_n = G_{n+1} X_n + X_n G_{n+1} (X^2) or 2 G_{n+1} - (G_{n+1} X_n + X_n G_{n+1})
-    (2X - X^2); finally dTr[X_L G]/dH = -G_0/(eps_max - eps_min).
+    G_L = sym(G); for the layer that made X_{n+1} from X_n through T_n (T_n = X_n
+    in the plain chain), G_n = a_n (G_{n+1} T_n + T_n G_{n+1}) (X^2) or
+    a_n (2 G_{n+1} - (G_{n+1} T_n + T_n G_{n+1})) (2X - X^2); finally
+    dTr[X_L G]/dH = -G_0/(eps_max - eps_min).
     """
+    a_of = (lambda k: 1.0) if alphas is None else (lambda k: alphas[k])
     X = input_layer(H, eps_min, eps_max)
+    n = X.shape[0]
     xs = [X]
-    for c in choices[:-1] if len(choices) else []:
-        X = apply_layer(X, c)
+    for k, c in enumerate(choices[:-1] if len(choices) else []):
+        X = apply_layer(X, c, a_of(k))
         xs.append(X)
     Gb = 0.5 * (np.asarray(G, np.float64) + np.asarray(G, np.float64).T)
-    for n in range(len(choices) - 1, -1, -1):
-        P = Gb @ xs[n]
+    for k in range(len(choices) - 1, -1, -1):
+        a = a_of(k)
+        T = a * xs[k] + (1.0 - a) * np.eye(n) if choices[k] == SQUARE else a * xs[k]
+        P = Gb @ T
         P = P + P.T
-        Gb = P if choices[n] == SQUARE else 2.0 * Gb - P
+        Gb = a * P if choices[k] == SQUARE else a * (2.0 * Gb - P)
     return -Gb / (eps_max - eps_min)
 
 
 def chain_derivative_eigenbasis(H: np.ndarray, H1: np.ndarray, choices: Sequence[int],
-                                eps_min: float, eps_max: float) -> np.ndarray:
+                                eps_min: float, eps_max: float, gap=None) -> np.ndarray:
     """Exact Frechet derivative of the fixed-sign chain via divided differences.
 
     With H = C diag(eps) C^T and the chain polynomial p acting on
@@ -268,7 +345,7 @@ def chain_derivative_eigenbasis(H: np.ndarray, H1: np.ndarray, choices: Sequence
     Phi_ii = -p'(x_i)/(eps_max - eps_min).
     """
     lam, C = np.linalg.eigh(np.asarray(H, np.float64))
-    p, _, _, dp = scalar_sp2(lam, 0, eps_min, eps_max, choices=list(choices))
+    p, _, _, dp = scalar_sp2(lam, 0, eps_min, eps_max, choices=list(choices), gap=gap)
     de = lam[:, None] - lam[None, :]
     dpv = p[:, None] - p[None, :]
     close = np.abs(de) <= 1e-12 * max(1.0, np.max(np.abs(lam)))

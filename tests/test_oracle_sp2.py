@@ -204,3 +204,109 @@ def test_refinement_of_perturbed_density(c0_small):
     assert abs(np.trace(X) - c0_small.n_occ) < 1e-9
     D = density.density_matrix(c0_small.H, c0_small.n_occ)
     assert np.linalg.norm(X - D) / np.sqrt(c0_small.n) < 1e-6
+
+
+# -- accelerated chain (estimated HOMO / LUMO interval) ------------------------------
+
+def test_golden_accelerated_layers():
+    g = load("sp2_accel_diag.txt")
+    H = np.diag(g["H_diag"])
+    gap = tuple(g["gap"])
+    r = sp2.sp2(H, int(g["n_occ"]), bounds=(0.0, 1.0), gap=gap, keep_layers=True)
+    assert r.choices[:2] == [int(c) for c in g["choices"]]
+    np.testing.assert_allclose(r.alphas[:2], g["alpha"], rtol=1e-15)
+    np.testing.assert_allclose(np.diag(r.layers_X[1]), g["X1_diag_times_256"] / 256, atol=1e-15)
+    np.testing.assert_allclose(np.diag(r.layers_X[2]), g["X2_diag_times_142129"] / 142129, atol=1e-15)
+    # the tracked ends of the interval are the images of the estimated eigenvalues
+    assert r.gap_images[1] == pytest.approx((135 / 256, 15 / 16), abs=1e-15)
+    assert r.gap_images[2] == pytest.approx(((135 / 377) ** 2, (345 / 377) ** 2), abs=1e-15)
+    np.testing.assert_allclose(r.D, np.diag([0, 0, 1, 1]), atol=1e-6)
+
+
+def test_accelerated_with_whole_range_is_the_plain_chain(c0_small):
+    lo, hi = sp2.gershgorin_bounds(c0_small.H)
+    plain = sp2.sp2(c0_small.H, c0_small.n_occ)
+    acc = sp2.sp2(c0_small.H, c0_small.n_occ, gap=(lo, hi))
+    assert acc.choices == plain.choices and set(acc.alphas) == {1.0}
+    assert np.array_equal(acc.D, plain.D)
+
+
+@pytest.fixture(scope="module")
+def accel_case():
+    ham = inputs.gapped_random(96, 40, np.random.default_rng(41), occ_range=(-1.0, -0.02),
+                               virt_range=(0.02, 1.0))
+    gap = (ham.eigvals[ham.n_occ - 1], ham.eigvals[ham.n_occ])
+    return ham, gap
+
+
+def test_accelerated_chain_converges_in_fewer_layers(accel_case):
+    ham, gap = accel_case
+    plain = sp2.sp2(ham.H, ham.n_occ)
+    acc = sp2.sp2(ham.H, ham.n_occ, gap=gap)
+    ref = density.density_matrix(ham.H, ham.n_occ)
+    assert acc.converged and acc.stop_reason == sp2.STOP_TOL
+    assert np.linalg.norm(acc.D - ref) < 1e-6
+    assert acc.layers <= 0.7 * plain.layers
+    assert all(1.0 <= a <= 2.0 for a in acc.alphas)
+
+
+def test_accelerated_images_follow_the_eigenvectors(accel_case):
+    # With the exact HOMO / LUMO as the estimate, the tracked interval ends are the
+    # Rayleigh quotients of the HOMO and LUMO eigenvectors in every layer.
+    ham, gap = accel_case
+    r = sp2.sp2(ham.H, ham.n_occ, gap=gap, keep_layers=True)
+    c_homo = ham.eigvecs[:, ham.n_occ - 1]
+    c_lumo = ham.eigvecs[:, ham.n_occ]
+    for X, (x_lumo, x_homo) in zip(r.layers_X, r.gap_images):
+        assert c_lumo @ X @ c_lumo == pytest.approx(x_lumo, abs=1e-11)
+        assert c_homo @ X @ c_homo == pytest.approx(x_homo, abs=1e-11)
+
+
+def test_accelerated_matrix_chain_matches_scalar_chain(accel_case):
+    ham, gap = accel_case
+    r = sp2.sp2(ham.H, ham.n_occ, gap=gap)
+    p, stats, reason, _ = sp2.scalar_sp2(ham.eigvals, ham.n_occ, r.eps_min, r.eps_max, gap=gap)
+    assert [s.choice for s in stats[1:]] == r.choices and reason == r.stop_reason
+    for a, b in zip(stats, r.stats):
+        assert a.trace == pytest.approx(b.trace, abs=1e-10)
+        assert a.trace_sq == pytest.approx(b.trace_sq, abs=1e-10)
+
+
+@pytest.mark.parametrize("how", ["wider", "narrower", "shifted_up", "shifted_down"])
+def test_accelerated_any_overlapping_interval_converges(accel_case, how):
+    ham, (e_homo, e_lumo) = accel_case
+    w = e_lumo - e_homo
+    est = {"wider": (e_homo - 3 * w, e_lumo + 3 * w), "narrower": (e_homo + 0.3 * w, e_lumo - 0.3 * w),
+           "shifted_up": (e_homo + 0.6 * w, e_lumo + 0.6 * w),
+           "shifted_down": (e_homo - 0.6 * w, e_lumo - 0.6 * w)}[how]
+    r = sp2.sp2(ham.H, ham.n_occ, gap=est)
+    assert r.converged
+    assert np.linalg.norm(r.D - density.density_matrix(ham.H, ham.n_occ)) < 1e-6
+
+
+def test_accelerated_interval_outside_the_gap_fails(accel_case):
+    # An interval that misses the gap (between the two highest occupied levels)
+    # breaks the ordering of the images: the chain no longer reaches theta(mu I - H).
+    ham, _ = accel_case
+    k = ham.n_occ
+    r = sp2.sp2(ham.H, k, gap=(ham.eigvals[k - 3], ham.eigvals[k - 2]))
+    ref = density.density_matrix(ham.H, k)
+    assert not r.converged or np.linalg.norm(r.D - ref) > 1e-3
+
+
+def test_accelerated_response_and_adjoint(accel_case):
+    ham, gap = accel_case
+    r = sp2.sp2(ham.H, ham.n_occ, gap=gap)
+    rng = np.random.default_rng(42)
+    H1 = inputs.symmetric_gaussian(ham.n, rng) * 0.05
+    G = inputs.symmetric_gaussian(ham.n, rng)
+    a = sp2.chain_response(ham.H, H1, r.choices, r.eps_min, r.eps_max, alphas=r.alphas)
+    b = sp2.chain_derivative_eigenbasis(ham.H, H1, r.choices, r.eps_min, r.eps_max, gap=gap)
+    np.testing.assert_allclose(a, b, atol=1e-8)
+    np.testing.assert_allclose(a, density.response(ham.H, H1, ham.n_occ), atol=1e-5)
+    h = 1e-6
+    run = lambda s: sp2.sp2(ham.H + s * H1, ham.n_occ, bounds=(r.eps_min, r.eps_max), choices=r.choices,
+                            gap=gap).D
+    np.testing.assert_allclose(a, (run(h) - run(-h)) / (2 * h), atol=1e-5)
+    grad = sp2.chain_adjoint(ham.H, G, r.choices, r.eps_min, r.eps_max, alphas=r.alphas)
+    assert np.sum(H1 * grad) == pytest.approx(np.sum(G * a), rel=1e-10)
