@@ -51,7 +51,7 @@ extern "C" {
 typedef enum {
     SP2_OK = 0,
     SP2_ERR_ARG = 1,            /* invalid argument (size, n_occ, pointer, option) */
-    SP2_ERR_NONFINITE = 2,      /* H (or H1 / G) contains NaN or Inf */
+    SP2_ERR_NONFINITE = 2,      /* H (or H1 / G) holds NaN, Inf or a magnitude >= 2^128 */
     SP2_ERR_NOT_CONVERGED = 3,  /* max_layers reached before the stop rule fired; output holds the last layer */
     SP2_ERR_TIMEOUT = 4,        /* a device-side wait gave up after timeout_ms */
     SP2_ERR_CUDA = 5,           /* a CUDA runtime or driver call failed */
@@ -86,6 +86,8 @@ typedef struct {
     double idem;      /* Tr X_n - ||X_n||_F^2 = sum_i lambda_i (1 - lambda_i) */
     int choice;       /* SP2_CHOICE_* that produced X_n */
     int reserved;
+    double alpha;     /* expansion a_n of the layer that produced X_n (1 in the plain chain
+                         and for the input layer; see sp2_opts.accelerate) */
 } sp2_layer_stat;
 
 /* Result record, caller-owned host memory.  `layer` may be NULL; otherwise it
@@ -124,6 +126,23 @@ typedef struct {
                              holds at once: work running concurrently on the same GPU can
                              deny that residency, and the call then ends with
                              SP2_ERR_TIMEOUT after timeout_ms) */
+    int accelerate;       /* 1 = accelerated chain from an estimated interval [eps_homo, eps_lumo]
+                             between the highest occupied and lowest unoccupied eigenvalue
+                             (section "GPU and tensor core performance" notes the saving of up
+                             to half the layers and leaves the scheme out).  Reading: before each
+                             layer X is expanded affinely, T = a X + (1 - a) I with
+                             a = 2/(2 - x_lumo) before X^2 and T = a X with a = 2/(1 + x_homo)
+                             before 2X - X^2, where x_lumo, x_homo are the images of eps_lumo,
+                             eps_homo under the input layer and follow every layer; the branch is
+                             still chosen by the trace rule.  The result is theta(mu I - H)
+                             whenever the interval overlaps the gap, i.e. eps_lumo is above the
+                             true HOMO and eps_homo below the true LUMO; the closer the interval
+                             is to the gap, the fewer the layers.  Requires
+                             eps_homo < eps_lumo (else SP2_ERR_ARG); sp2_density, sp2_response
+                             and sp2_adjoint only (sp2_density_batched: SP2_ERR_ARG).  Response
+                             and adjoint replay the forward run's a_n from its stats. */
+    double eps_homo;
+    double eps_lumo;
 } sp2_opts;
 
 /* Fill `o` with the defaults. */

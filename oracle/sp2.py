@@ -191,14 +191,15 @@ def _stat(X: np.ndarray, choice: int) -> LayerStat:
 def sp2(H: np.ndarray, n_occ: int, tol: float = DEFAULT_TOL,
         max_layers: int = DEFAULT_MAX_LAYERS, bounds=None,
         choices: Optional[Sequence[int]] = None, keep_layers: bool = False,
-        gap=None) -> SP2Result:
+        gap=None, alphas: Optional[Sequence[float]] = None) -> SP2Result:
     """Run the DNN-SP2 chain on H in float64.
 
     ``choices`` replays a given sign sequence exactly (used to follow a
     sequence taken by another implementation); the stop rule is then only
     evaluated for the report.  With ``keep_layers`` the result carries every X_n in
     ``result.layers_X``.  ``gap = (eps_homo, eps_lumo)`` runs the accelerated
-    chain (module docstring).
+    chain (module docstring); ``alphas`` replays given expansions a_n together with
+    ``choices``.
     """
     H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
@@ -211,16 +212,16 @@ def sp2(H: np.ndarray, n_occ: int, tol: float = DEFAULT_TOL,
     X = input_layer(H, eps_min, eps_max)
     x_lumo, x_homo = gap_images(gap, eps_min, eps_max)
     stats = [_stat(X, INPUT)]
-    alphas = []
+    used = []  # a_n of every layer applied
     images = [(x_lumo, x_homo)]
     kept = [X] if keep_layers else None
 
     def step(c):
         nonlocal X, x_lumo, x_homo
-        a = expansion(c, x_lumo, x_homo)
+        a = expansion(c, x_lumo, x_homo) if alphas is None else float(alphas[len(stats) - 1])
         X = apply_layer(X, c, a)
         x_lumo, x_homo = scalar_layer(x_lumo, c, a), scalar_layer(x_homo, c, a)
-        alphas.append(a)
+        used.append(a)
         images.append((x_lumo, x_homo))
         stats.append(_stat(X, c))
         if keep_layers:
@@ -236,7 +237,7 @@ def sp2(H: np.ndarray, n_occ: int, tol: float = DEFAULT_TOL,
         while not reason:
             step(layer_choice(stats[-1].trace, stats[-1].trace_sq, n_occ))
             reason = stop_check([s.idem for s in stats], tol, max_layers)
-    res = SP2Result(X, stats, reason, reason in (STOP_TOL, STOP_STALL), eps_min, eps_max, alphas)
+    res = SP2Result(X, stats, reason, reason in (STOP_TOL, STOP_STALL), eps_min, eps_max, used)
     res.layers_X = kept
     res.gap_images = images  # (x_lumo, x_homo) after each layer, entry 0 for X_0
     return res

@@ -187,12 +187,14 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
     c.take(sizeof(int2) * tiles);
     c.take(64);                           // barrier + err
     c.take(sizeof(int) * (MAX_L + 1));    // forced choices
+    c.take(sizeof(double) * (MAX_L + 1)); // forced expansions
+    c.take(sizeof(InstCtl) * B);          // control blocks
+    c.take(sizeof(InstCtl) * B);          // their initial state, copied in before every launch
     const int initb = init_blocks_host(pl.max_np);
     for (int i = 0; i < B; ++i) {
         const int np = round_up(pl.inst[i].n, PAD);
         const size_t mat = (size_t)np * np;
         const int cap = std::max(parts_for(pl.path, np, pl.cg), initb);
-        c.take(sizeof(InstCtl));
         c.take(sizeof(Part) * cap);
         c.take(sizeof(Part) * cap);
         c.take(sizeof(double2) * FIN_BLOCKS_MAX);
@@ -228,6 +230,7 @@ void fill_stats(sp2_stats *st, const InstCtl &ctl) {
             st->layer[k].idem = ctl.stat[k].idem;
             st->layer[k].choice = ctl.stat[k].choice;
             st->layer[k].reserved = 0;
+            st->layer[k].alpha = ctl.stat[k].alpha;
         }
     }
 }
@@ -246,6 +249,7 @@ void fill_trivial_stats(sp2_stats *st, int n, double n_occ) {
         st->layer[0].idem = 0.0;
         st->layer[0].choice = SP2_CHOICE_INPUT;
         st->layer[0].reserved = 0;
+        st->layer[0].alpha = 1.0;
     }
 }
 
@@ -265,18 +269,35 @@ int status_rank(int s) {
         }                                      \
     } while (0)
 
-sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws_bytes, cudaStream_t s) {
-    const int B = (int)pl.inst.size();
-    if (B == 0) return SP2_OK;
+// Everything one launch of the path needs, laid out in device memory.  prepare()
+// builds and uploads it, enqueue() puts one solve on a stream (device work only:
+// control-block reset, barrier reset, kernels -- so it can be captured in a CUDA
+// graph and replayed), collect() reads the control blocks back.
+struct Prepared {
+    Plan pl;
+    sp2_opts o;
+    double tol = 0.0;
+    int grid = 0;
+    bool user_bounds = false;
+    InstDesc *d_inst = nullptr;
+    int2 *d_tiles = nullptr;
+    uint8_t *d_sync = nullptr;
+    InstCtl *d_ctl = nullptr;        // B live control blocks
+    InstCtl *d_ctl_init = nullptr;   // B initial control blocks
+    std::vector<InstCtl> h_ctl;
+    std::vector<std::pair<float *, float *>> copy_back;  // (host, device staging)
+    std::vector<size_t> copy_back_n;
+};
+
+// Tensor-core tile shape and persistent grid for the plan: CTA pairs (M = 256)
+// when the device can co-schedule them, else single CTAs; `want` forces one.
+sp2_status choose_launch(Plan &pl, int want, int &grid) {
     DeviceInfo di = query_device();
     if (di.err != cudaSuccess) return SP2_ERR_CUDA;
     if (di.major != 10 || di.minor != 3) return SP2_ERR_UNSUPPORTED;
     if (pl.path == PATH_TC && !get_encode_fn()) return SP2_ERR_UNSUPPORTED;
-    // Tensor-core tile shape: CTA pairs (M = 256) when the device can co-schedule
-    // them for a cooperative launch, else single CTAs.
-    int grid = 0;
+    grid = 0;
     if (pl.path == PATH_TC) {
-        const int want = o.cta_group;
         if (want == 0 || want == 2) {
             grid = tc_grid_size(2, di.sm);
             pl.cg = 2;
@@ -292,15 +313,20 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
         if (per_sm <= 0) return SP2_ERR_UNSUPPORTED;
         grid = per_sm * di.sm;
     }
+    return SP2_OK;
+}
 
-    Arena arena(s);
-    const size_t need = plan_bytes(pl);
-    if (ws && ws_bytes < need) return SP2_ERR_ARG;
-    if (ws && ((uintptr_t)ws & 255)) return SP2_ERR_ARG;
-    if (!ws) {
-        ws = arena.get(need);
-        if (!ws) return SP2_ERR_NOMEM;
-    }
+// Lay out the workspace (`ws`, at least plan_bytes(pl) bytes), build the
+// descriptors, tile tables and tensor maps and upload them with the initial
+// control blocks.  Host-resident matrices are staged through device memory
+// (the workspace tail, else `arena`) when `staging_ok`; otherwise they are an
+// argument error.
+sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t ws_bytes, cudaStream_t s,
+                   Arena &arena, bool staging_ok) {
+    Plan &pl = P.pl;
+    P.o = o;
+    P.tol = tol;
+    const int B = (int)pl.inst.size();
     Carver c(ws);
     InstDesc *d_inst = (InstDesc *)c.take(sizeof(InstDesc) * B);
     std::vector<std::vector<int2>> tiles(B);
@@ -312,14 +338,18 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     int2 *d_tiles = (int2 *)c.take(sizeof(int2) * total_tiles);
     uint8_t *d_sync = (uint8_t *)c.take(64);
     int *d_forced = (int *)c.take(sizeof(int) * (MAX_L + 1));
+    double *d_forced_alpha = (double *)c.take(sizeof(double) * (MAX_L + 1));
+    InstCtl *d_ctl = (InstCtl *)c.take(sizeof(InstCtl) * B);
+    InstCtl *d_ctl_init = (InstCtl *)c.take(sizeof(InstCtl) * B);
 
     std::vector<InstDesc> h_inst(B);
-    std::vector<InstCtl> h_ctl(B);
+    std::vector<InstCtl> &h_ctl = P.h_ctl;
+    h_ctl.assign(B, InstCtl());
     std::vector<int2> h_tiles;
     std::vector<std::vector<CUtensorMap>> h_xmaps(B), h_ymaps(B);
     std::vector<CUtensorMap *> d_xmaps(B, nullptr), d_ymaps(B, nullptr);
-    std::vector<InstCtl *> d_ctl(B);
     std::vector<int> forced;
+    std::vector<double> forced_alpha;
     const int initb = init_blocks_host(pl.max_np);
     bool user_bounds = o.user_bounds != 0;
 
@@ -340,8 +370,7 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
         d.nslots_x = pl.slots[i];
         d.part_cap = std::max(d.parts, initb);
         d.fin_blocks = FIN_BLOCKS_MAX;
-        d_ctl[i] = (InstCtl *)c.take(sizeof(InstCtl));
-        d.ctl = d_ctl[i];
+        d.ctl = d_ctl + i;
         d.part[0] = (Part *)c.take(sizeof(Part) * d.part_cap);
         d.part[1] = (Part *)c.take(sizeof(Part) * d.part_cap);
         d.fin_part = (double2 *)c.take(sizeof(double2) * FIN_BLOCKS_MAX);
@@ -391,6 +420,15 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
             for (int k = 0; k < sp.fwd->layers; ++k) forced[k] = sp.fwd->layer[k + 1].choice;
             d.nforced = sp.fwd->layers;
             d.forced = d_forced;
+            // An accelerated forward run is replayed with its own expansions.
+            bool plain = true;
+            forced_alpha.assign(sp.fwd->layers, 1.0);
+            for (int k = 0; k < sp.fwd->layers; ++k) {
+                forced_alpha[k] = sp.fwd->layer[k + 1].alpha;
+                plain = plain && forced_alpha[k] == 1.0;
+            }
+            if (!plain) d.forced_alpha = d_forced_alpha;
+            else forced_alpha.clear();
         } else if (sp.choices) {
             forced.assign(sp.choices, sp.choices + sp.nchoices);
             d.nforced = sp.nchoices;
@@ -399,69 +437,78 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
             ctl.eps_min = o.eps_min;
             ctl.eps_max = o.eps_max;
         }
+        if (o.accelerate && !sp.fwd && !sp.choices) {
+            d.accel = 1;
+            d.gap_homo = o.eps_homo;
+            d.gap_lumo = o.eps_lumo;
+        }
         d.H = sp.H;
         d.H1 = sp.H1;
         d.out = sp.D;
         d.out1 = sp.D1;
     }
 
-    // Stage host-resident inputs and outputs through device memory: from the
-    // tail of the caller's workspace when it has room, else a stream-ordered
-    // allocation freed before the call returns.
+    // Host-resident inputs and outputs go through device memory: the tail of
+    // the caller's workspace when it has room, else a stream-ordered allocation
+    // freed before the call returns.
     const size_t ws_end = ws_bytes;
     auto staging = [&](size_t bytes) -> void * {
         const size_t start = (c.off + 255) & ~(size_t)255;
         if (ws_end && start + bytes <= ws_end) return c.take(bytes);
         return arena.get(bytes);
     };
-    std::vector<std::pair<float *, float *>> copy_back;  // (host, device staging)
-    std::vector<size_t> copy_back_n;
     for (int i = 0; i < B; ++i) {
         InstSpec &sp = pl.inst[i];
         InstDesc &d = h_inst[i];
         const size_t nn = (size_t)sp.n * sp.n;
-        if (sp.H && !is_device_ptr(sp.H)) {
+        const bool hH = sp.H && !is_device_ptr(sp.H), hH1 = sp.H1 && !is_device_ptr(sp.H1);
+        const bool hX0 = sp.X0 && !is_device_ptr(sp.X0), hD = sp.D && !is_device_ptr(sp.D);
+        const bool hD1 = sp.D1 && !is_device_ptr(sp.D1);
+        if (!staging_ok && (hH || hH1 || hX0 || hD || hD1)) return SP2_ERR_ARG;
+        if (hH) {
             double *t = (double *)staging(nn * 8);
             if (!t) return SP2_ERR_NOMEM;
             CK(cudaMemcpyAsync(t, sp.H, nn * 8, cudaMemcpyHostToDevice, s));
             d.H = t;
         }
-        if (sp.H1 && !is_device_ptr(sp.H1)) {
+        if (hH1) {
             double *t = (double *)staging(nn * 8);
             if (!t) return SP2_ERR_NOMEM;
             CK(cudaMemcpyAsync(t, sp.H1, nn * 8, cudaMemcpyHostToDevice, s));
             d.H1 = t;
         }
-        if (sp.X0 && !is_device_ptr(sp.X0)) {
+        if (hX0) {
             float *t = (float *)staging(nn * 4);
             if (!t) return SP2_ERR_NOMEM;
             CK(cudaMemcpyAsync(t, sp.X0, nn * 4, cudaMemcpyHostToDevice, s));
             sp.X0 = t;
         }
-        if (sp.D && !is_device_ptr(sp.D)) {
+        if (hD) {
             float *t = (float *)staging(nn * 4);
             if (!t) return SP2_ERR_NOMEM;
-            copy_back.push_back({sp.D, t});
-            copy_back_n.push_back(nn);
+            P.copy_back.push_back({sp.D, t});
+            P.copy_back_n.push_back(nn);
             d.out = t;
         }
-        if (sp.D1 && !is_device_ptr(sp.D1)) {
+        if (hD1) {
             float *t = (float *)staging(nn * 4);
             if (!t) return SP2_ERR_NOMEM;
-            copy_back.push_back({sp.D1, t});
-            copy_back_n.push_back(nn);
+            P.copy_back.push_back({sp.D1, t});
+            P.copy_back_n.push_back(nn);
             d.out1 = t;
         }
     }
 
-    // Upload descriptors, tables and control blocks.
+    // Upload descriptors, tables, tensor maps and the initial control blocks.
     CK(cudaMemcpyAsync(d_inst, h_inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_tiles, h_tiles.data(), sizeof(int2) * h_tiles.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(d_sync, 0, 64, s));
     if (!forced.empty())
         CK(cudaMemcpyAsync(d_forced, forced.data(), sizeof(int) * forced.size(), cudaMemcpyHostToDevice, s));
+    if (!forced_alpha.empty())
+        CK(cudaMemcpyAsync(d_forced_alpha, forced_alpha.data(), sizeof(double) * forced_alpha.size(),
+                           cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_ctl_init, h_ctl.data(), sizeof(InstCtl) * B, cudaMemcpyHostToDevice, s));
     for (int i = 0; i < B; ++i) {
-        CK(cudaMemcpyAsync(d_ctl[i], &h_ctl[i], sizeof(InstCtl), cudaMemcpyHostToDevice, s));
         if (d_xmaps[i])
             CK(cudaMemcpyAsync(d_xmaps[i], h_xmaps[i].data(), h_xmaps[i].size() * sizeof(CUtensorMap),
                                cudaMemcpyHostToDevice, s));
@@ -469,7 +516,97 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
             CK(cudaMemcpyAsync(d_ymaps[i], h_ymaps[i].data(), h_ymaps[i].size() * sizeof(CUtensorMap),
                                cudaMemcpyHostToDevice, s));
     }
+    P.user_bounds = user_bounds;
+    P.d_inst = d_inst;
+    P.d_tiles = d_tiles;
+    P.d_sync = d_sync;
+    P.d_ctl = d_ctl;
+    P.d_ctl_init = d_ctl_init;
+    return SP2_OK;
+}
 
+// One solve on stream s: reset, input layer, the persistent layer kernel, the
+// output.  ev (optional, 4 events) brackets the phases.
+sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
+    const Plan &pl = P.pl;
+    const int B = (int)pl.inst.size();
+    CK(cudaMemcpyAsync(P.d_ctl, P.d_ctl_init, sizeof(InstCtl) * B, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(P.d_sync, 0, 64, s));
+    if (ev) CK(cudaEventRecord(ev[0], s));
+    if (pl.mode == MODE_APPLY) {
+        CK(launch_init_x_from(P.d_inst, pl.inst[0].X0, pl.max_np, pl.path, pl.precision, s));
+    } else {
+        CK(launch_gershgorin(P.d_inst, B, pl.max_n, P.user_bounds, s));
+        CK(launch_init_x(P.d_inst, B, pl.max_np, pl.path, pl.precision, P.user_bounds, s));
+    }
+    if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
+        CK(launch_maxabs(P.d_inst, B, pl.max_n, s));
+        CK(launch_init_y(P.d_inst, pl.mode, pl.precision, s));
+    }
+    RunParams rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.inst = P.d_inst;
+    rp.tiles = P.d_tiles;
+    rp.barrier = (unsigned int *)P.d_sync;
+    rp.err = (int *)(P.d_sync + 4);
+    rp.tol = P.tol;
+    rp.timeout_ns = (unsigned long long)(P.o.timeout_ms * 1e6);
+    rp.B = B;
+    rp.mode = pl.mode;
+    rp.precision = pl.precision;
+    rp.max_layers = P.o.max_layers;
+    rp.test_hook = P.o.test_hook;
+    if (ev) CK(cudaEventRecord(ev[1], s));
+    CK(pl.path == PATH_TC ? launch_tc_persistent(rp, pl.cg, P.grid, s) : launch_simt_persistent(rp, P.grid, s));
+    if (ev) CK(cudaEventRecord(ev[2], s));
+    CK(launch_finalize(P.d_inst, B, pl.max_n, pl.mode == MODE_APPLY ? MODE_DENSITY : pl.mode, s));
+    if (ev) CK(cudaEventRecord(ev[3], s));
+    return SP2_OK;
+}
+
+// Read the control blocks back (synchronises s) and fill the callers' stats.
+sp2_status collect(Prepared &P, cudaStream_t s, const float *ph) {
+    const Plan &pl = P.pl;
+    const int B = (int)pl.inst.size();
+    for (size_t k = 0; k < P.copy_back.size(); ++k)
+        CK(cudaMemcpyAsync(P.copy_back[k].first, P.copy_back[k].second, P.copy_back_n[k] * 4,
+                           cudaMemcpyDeviceToHost, s));
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, P.d_sync + 4, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(P.h_ctl.data(), P.d_ctl, sizeof(InstCtl) * B, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h_err) return (sp2_status)h_err;
+    int worst = SP2_OK;
+    for (int i = 0; i < B; ++i) {
+        fill_stats(pl.inst[i].st, P.h_ctl[i]);
+        if (pl.inst[i].st) {
+            for (int k = 0; k < 4; ++k) pl.inst[i].st->phase_ms[k] = ph ? ph[k] : 0.0f;
+            pl.inst[i].st->cta_group = (pl.path == PATH_TC) ? pl.cg : 0;
+        }
+        int stt = P.h_ctl[i].status;
+        if (P.h_ctl[i].nonfinite) stt = SP2_ERR_NONFINITE;
+        if (status_rank(stt) > status_rank(worst)) worst = stt;
+    }
+    return (sp2_status)worst;
+}
+
+sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws_bytes, cudaStream_t s) {
+    const int B = (int)pl.inst.size();
+    if (B == 0) return SP2_OK;
+    Prepared P;
+    P.pl = pl;
+    sp2_status r = choose_launch(P.pl, o.cta_group, P.grid);
+    if (r != SP2_OK) return r;
+    Arena arena(s);
+    const size_t need = plan_bytes(P.pl);
+    if (ws && ws_bytes < need) return SP2_ERR_ARG;
+    if (ws && ((uintptr_t)ws & 255)) return SP2_ERR_ARG;
+    if (!ws) {
+        ws = arena.get(need);
+        if (!ws) return SP2_ERR_NOMEM;
+    }
+    r = prepare(P, o, tol, ws, ws_bytes, s, arena, true);
+    if (r != SP2_OK) return r;
     // Optional per-phase device timing on the call's stream.
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     struct EvGuard {
@@ -481,67 +618,20 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     } ev_guard{ev};
     if (o.profile)
         for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ev[k]));
-    if (o.profile) CK(cudaEventRecord(ev[0], s));
-
-    // Input layer.
-    if (pl.mode == MODE_APPLY) {
-        CK(launch_init_x_from(d_inst, pl.inst[0].X0, pl.max_np, pl.path, pl.precision, s));
-    } else {
-        CK(launch_gershgorin(d_inst, B, pl.max_n, user_bounds, s));
-        CK(launch_init_x(d_inst, B, pl.max_np, pl.path, pl.precision, user_bounds, s));
-    }
-    if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
-        CK(launch_maxabs(d_inst, B, pl.max_n, s));
-        CK(launch_init_y(d_inst, pl.mode, pl.precision, s));
-    }
-
-    // The layer loop.
-    RunParams rp;
-    memset(&rp, 0, sizeof(rp));
-    rp.inst = d_inst;
-    rp.tiles = d_tiles;
-    rp.barrier = (unsigned int *)d_sync;
-    rp.err = (int *)(d_sync + 4);
-    rp.tol = tol;
-    rp.timeout_ns = (unsigned long long)(o.timeout_ms * 1e6);
-    rp.B = B;
-    rp.mode = pl.mode;
-    rp.precision = pl.precision;
-    rp.max_layers = o.max_layers;
-    rp.test_hook = o.test_hook;
-    if (o.profile) CK(cudaEventRecord(ev[1], s));
-    CK(pl.path == PATH_TC ? launch_tc_persistent(rp, pl.cg, grid, s) : launch_simt_persistent(rp, grid, s));
-    if (o.profile) CK(cudaEventRecord(ev[2], s));
-
-    CK(launch_finalize(d_inst, B, pl.max_n, pl.mode == MODE_APPLY ? MODE_DENSITY : pl.mode, s));
-    if (o.profile) CK(cudaEventRecord(ev[3], s));
-    for (size_t k = 0; k < copy_back.size(); ++k)
-        CK(cudaMemcpyAsync(copy_back[k].first, copy_back[k].second, copy_back_n[k] * 4, cudaMemcpyDeviceToHost, s));
-    int h_err = 0;
-    CK(cudaMemcpyAsync(&h_err, d_sync + 4, 4, cudaMemcpyDeviceToHost, s));
-    for (int i = 0; i < B; ++i) CK(cudaMemcpyAsync(&h_ctl[i], d_ctl[i], sizeof(InstCtl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-
-    if (h_err) return (sp2_status)h_err;
+    r = enqueue(P, s, o.profile ? ev : nullptr);
+    if (r != SP2_OK) return r;
     float ph[4] = {0.f, 0.f, 0.f, 0.f};
+    r = collect(P, s, nullptr);
     if (o.profile) {
         CK(cudaEventElapsedTime(&ph[0], ev[0], ev[1]));
         CK(cudaEventElapsedTime(&ph[1], ev[1], ev[2]));
         CK(cudaEventElapsedTime(&ph[2], ev[2], ev[3]));
         CK(cudaEventElapsedTime(&ph[3], ev[0], ev[3]));
+        for (int i = 0; i < B; ++i)
+            if (P.pl.inst[i].st)
+                for (int k = 0; k < 4; ++k) P.pl.inst[i].st->phase_ms[k] = ph[k];
     }
-    int worst = SP2_OK;
-    for (int i = 0; i < B; ++i) {
-        fill_stats(pl.inst[i].st, h_ctl[i]);
-        if (pl.inst[i].st) {
-            for (int k = 0; k < 4; ++k) pl.inst[i].st->phase_ms[k] = ph[k];
-            pl.inst[i].st->cta_group = (pl.path == PATH_TC) ? pl.cg : 0;
-        }
-        int stt = h_ctl[i].status;
-        if (h_ctl[i].nonfinite) stt = SP2_ERR_NONFINITE;
-        if (status_rank(stt) > status_rank(worst)) worst = stt;
-    }
-    return (sp2_status)worst;
+    return r;
 }
 
 bool integral_occ(double n_occ, int n) {
@@ -556,6 +646,9 @@ sp2_status check_opts(const sp2_opts &o) {
     if (o.test_hook < 0 || o.test_hook > 1) return SP2_ERR_ARG;
     if (o.profile < 0 || o.profile > 1) return SP2_ERR_ARG;
     if (o.cta_group < 0 || o.cta_group > 2) return SP2_ERR_ARG;
+    if (o.accelerate < 0 || o.accelerate > 1) return SP2_ERR_ARG;
+    if (o.accelerate && !(std::isfinite(o.eps_homo) && std::isfinite(o.eps_lumo) && o.eps_homo < o.eps_lumo))
+        return SP2_ERR_ARG;
     return SP2_OK;
 }
 
@@ -764,6 +857,7 @@ sp2_status sp2_density_batched(int B, const double *const *H, const int *N, cons
                                float *const *D, sp2_stats *st, const sp2_opts *o, void *workspace, size_t ws_bytes,
                                void *stream) {
     if (B < 1 || !H || !N || !n_occ || !D) return SP2_ERR_ARG;
+    if (o && o->accelerate) return SP2_ERR_ARG;  // one interval cannot serve every instance
     std::vector<InstSpec> v(B);
     for (int b = 0; b < B; ++b) {
         v[b].n = N[b];
@@ -781,6 +875,7 @@ sp2_status sp2_apply_layers(const float *X0, int N, const int *choices, int n_la
         return SP2_ERR_ARG;
     for (int k = 0; k < n_layers; ++k)
         if (choices[k] != SP2_CHOICE_SQUARE && choices[k] != SP2_CHOICE_FLIP) return SP2_ERR_ARG;
+    if (o && o->accelerate) return SP2_ERR_ARG;  // the layers applied here are the plain ones
     std::vector<InstSpec> v(1);
     v[0].n = N;
     v[0].n_occ = 0.0;

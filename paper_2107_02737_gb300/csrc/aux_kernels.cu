@@ -12,6 +12,39 @@ namespace {
 
 constexpr int AUX_THREADS = 256;
 
+// ---------------------------------------------------------------------------
+// FP64 -> FP32 pairs with 32-bit integer operations only.  GB300 runs FP64
+// arithmetic and FP64 <-> FP32 conversions at a small fraction of its FP32 and
+// integer rates, so the HBM-bound kernels that read FP64 matrices unpack them
+// here.  split_f64(v, hi, lo24): hi = v with its mantissa truncated to 24
+// bits, lo24 = 2^24 x (the next 24 bits, truncated), so that
+// 0 <= |v| - (|hi| + 2^-24 |lo24|) < 2^-47 |v| for |v| >= 2^-98; below that
+// lo24 is 0 and the cut is < 2^-121.  The 2^24 keeps lo24 a normal float.
+// Values below 2^-126 give hi = 0; non-finite inputs and |v| >= 2^128 set `bad`.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_f64(double v, float &hi, float &lo24, int &bad) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned int h32 = (unsigned int)(b >> 32), l32 = (unsigned int)b;
+    const unsigned int sign = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7FFu);
+    if (e == 0x7FF) bad = 1;
+    const int e32 = e - 1023 + 127;
+    if (e == 0 || e32 <= 0 || e32 >= 255) {
+        hi = 0.0f;
+        lo24 = 0.0f;
+        if (e32 >= 255 && e != 0x7FF) bad = 1;
+        return;
+    }
+    // 52-bit mantissa m = [h32 & 0xFFFFF : l32]; hi keeps its top 23 bits.
+    const unsigned int mhi = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+    hi = __uint_as_float(sign | ((unsigned int)e32 << 23) | mhi);
+    // The remaining 29 bits (l32 & 0x1FFFFFFF) weigh 2^(e - 1023 - 52); times
+    // 2^24 that is the float exponent field e32 - 28.
+    const unsigned int rem = l32 & 0x1FFFFFFFu;
+    const float r = __uint2float_rz(rem) * __uint_as_float((unsigned int)(e32 > 28 ? e32 - 28 : 1) << 23);
+    lo24 = (e32 > 28) ? (sign ? -r : r) : 0.0f;
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
     // Fixed shuffle-down tree: lane 0 holds the sum, in the same order every run.
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -65,8 +98,13 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
     return r;
 }
 
-// Gershgorin discs: one warp per row, FP64 row sums of |H_ij|, j != i.  Each
-// lane keeps eight loads in flight and four partial sums (fixed order).
+// Gershgorin discs: one warp per row.  Each off-diagonal |H_ij| is unpacked
+// with integer operations into |hi| + 2^-24 |lo24|, which falls short of it by
+// less than 2^-47 relative (2^-121 absolute for tiny entries); the |hi| are
+// summed in compensated FP32 pairs and the |lo24| in FP32.  The radius is then
+// widened to r (1 + 2^-36) + 2^-50 |d| + N 2^-120, which covers the cut, the
+// sums and the rounding of d -/+ r, so the bounds contain every exact disc and
+// exceed it by about 2^-36 relative.  Centres and bounds are FP64.
 __global__ void __launch_bounds__(AUX_THREADS) k_gershgorin(InstDesc *inst) {
     const InstDesc &d = inst[blockIdx.y];
     const int n = d.n;
@@ -75,7 +113,8 @@ __global__ void __launch_bounds__(AUX_THREADS) k_gershgorin(InstDesc *inst) {
     int bad = 0;
     for (int row = blockIdx.x * (AUX_THREADS / 32) + w; row < n; row += gridDim.x * (AUX_THREADS / 32)) {
         const double *__restrict__ h = d.H + (size_t)row * n;
-        double r[4] = {0.0, 0.0, 0.0, 0.0};
+        FF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        float acc_lo = 0.0f;  // sum of the 2^24-scaled low parts
         for (int j0 = lane; j0 < n; j0 += 32 * 8) {
             double v[8];
 #pragma unroll
@@ -86,13 +125,19 @@ __global__ void __launch_bounds__(AUX_THREADS) k_gershgorin(InstDesc *inst) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int j = j0 + 32 * u;
-                bad |= !isfinite(v[u]);
-                r[u & 3] += (j != row) ? fabs(v[u]) : 0.0;
+                float a, b;
+                split_f64(v[u], a, b, bad);
+                if (j != row) {
+                    ff_add(acc[u & 1], fabsf(a));
+                    acc_lo += fabsf(b);
+                }
             }
         }
-        double rs = warp_sum_d((r[0] + r[1]) + (r[2] + r[3]));
+        double rs = warp_sum_d(ff_value(acc[0]) + ff_value(acc[1]) + (double)acc_lo * 0x1p-24);
         rs = __shfl_sync(0xffffffffu, rs, 0);
         const double dv = h[row];
+        if (!isfinite(dv)) bad = 1;
+        rs = rs * (1.0 + 0x1p-36) + fabs(dv) * 0x1p-50 + (double)n * 0x1p-120;
         lo = fmin(lo, dv - rs);
         hi = fmax(hi, dv + rs);
     }
@@ -112,11 +157,13 @@ __global__ void __launch_bounds__(AUX_THREADS) k_maxabs(InstDesc *inst) {
     const size_t total = (size_t)d.n * d.n;
     double m = 0.0;
     int bad = 0;
+    float mf = 0.0f;
     for (size_t e = (size_t)blockIdx.x * AUX_THREADS + threadIdx.x; e < total; e += (size_t)gridDim.x * AUX_THREADS) {
-        double v = d.H1[e];
-        bad |= !isfinite(v);
-        m = fmax(m, fabs(v));
+        float a, b;
+        split_f64(d.H1[e], a, b, bad);
+        mf = fmaxf(mf, fabsf(a) + fabsf(b) * 0x1p-24f);
     }
+    m = (double)mf;
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
     bad = __any_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0) {
@@ -145,6 +192,10 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
     const double delta = emax - emin;
     const bool degenerate = !(delta > 0.0) || !isfinite(delta) || d.ctl->nonfinite;
     const double inv = degenerate ? 0.0 : 1.0 / delta;
+    const float inv_hi = (float)inv;                 // 1/delta as a float pair
+    const float inv_lo = (float)(inv - (double)inv_hi);
+    const float inv_lo24 = inv_hi * 0x1p-24f;       // weight of the 2^24-scaled low part
+    int bad_unused = 0;
     float *__restrict__ xf = d.xf[0];
     uint16_t *__restrict__ op0 = d.xop;
     uint16_t *__restrict__ op1 = d.xop + (size_t)np * np;
@@ -163,7 +214,15 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
             for (int q = 0; q < 4; ++q) {
                 const int j = j0 + q;
                 float v = 0.0f;
-                if (i < n && j < n) v = (float)((((i == j) ? emax : 0.0) - hrow[j]) * inv);
+                if (i < n && j < n) {
+                    if (i == j) {
+                        v = (float)((emax - hrow[j]) * inv);  // FP64 on the N diagonal entries only
+                    } else {
+                        float a, b;  // -h / (eps_max - eps_min): one rounding of a sum of small terms
+                        split_f64(hrow[j], a, b, bad_unused);
+                        v = -fmaf(a, inv_hi, fmaf(a, inv_lo, b * inv_lo24));
+                    }
+                }
                 x[q] = v;
                 y[q] = (i == j && i < n) ? v - 0.5f : v;
                 if (i == j) ff_add(ft, v);
@@ -291,7 +350,11 @@ __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mo
     float ys = 0.0f;
     if (mode == MODE_RESPONSE) ys = (float)(1.0 / ctl->y_scale);
     if (mode == MODE_ADJOINT) ys = (float)(-1.0 / (ctl->y_scale * (ctl->eps_max - ctl->eps_min)));
-    double e = 0.0, tr = 0.0;
+    // Tr[D H]: each H_ij unpacked to an FP32 pair (h1 + 2^-24 h2), x * h1 split exactly
+    // into product and error (FMA), all summed in a compensated FP32 pair.
+    FF fe = {0.f, 0.f};
+    double tr = 0.0;
+    int bad_unused = 0;
     for (int i = blockIdx.x; i < n; i += d.fin_blocks) {
         const float *__restrict__ xrow = X + (size_t)i * np;
         const size_t base = (size_t)i * n;
@@ -303,11 +366,19 @@ __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mo
                 tr += x;
             }
             if (out) out[base + j] = x;
-            if (H && j >= i) e += (j == i ? 1.0 : 2.0) * (double)x * H[base + j];
+            if (H && j >= i) {
+                float h1, h2;
+                split_f64(H[base + j], h1, h2, bad_unused);
+                const float wgt = (j == i) ? 1.0f : 2.0f;
+                const float p = __fmul_rn(x, h1);
+                const float perr = __fmaf_rn(x, h1, -p);
+                ff_add(fe, __fmul_rn(wgt, p));
+                fe.c = __fadd_rn(fe.c, __fmul_rn(wgt, __fmaf_rn(x, h2 * 0x1p-24f, perr)));
+            }
             if (second) out1[base + j] = Y[(size_t)i * np + j] * ys;
         }
     }
-    double2 s = block_sum2(e, tr);
+    double2 s = block_sum2(ff_value(fe), tr);
     if (threadIdx.x == 0) d.fin_part[blockIdx.x] = s;
 }
 

@@ -158,6 +158,9 @@ struct RoundCtl {
     double coff[MAX_BATCH];          // c_n: true X_n = stored X_n + c_n I
     signed char chist[MAX_L + 2];    // adjoint (B = 1): choice that produced X_n
     double chist_c[MAX_L + 2];       // adjoint (B = 1): c_n per layer
+    float chist_a[MAX_L + 2];        // adjoint (B = 1): a_n of the layer that produced X_n
+    float alpha[MAX_BATCH];          // a of the layer computed this round (1 = plain)
+    float xl[MAX_BATCH], xh[MAX_BATCH];  // accelerated chain: images of eps_lumo, eps_homo
 };
 
 __host__ __device__ __forceinline__ int layer_rule(double t, double q, double n_occ) {
@@ -180,8 +183,24 @@ __device__ __forceinline__ void round_ctl_init(RoundCtl &rc, const RunParams &p)
         rc.ehist[i][0] = rc.ehist[i][1] = 0.0;
         rc.wprev[i] = 0.0;
         rc.coff[i] = 0.0;
+        rc.alpha[i] = 1.0f;
+        // Images of the estimated interval under the input layer, clipped to
+        // [0, 1]; (0, 1) keeps every a_n = 1, the plain chain.
+        float xl = 0.0f, xh = 1.0f;
+        const InstDesc &d = p.inst[i];
+        if (d.accel) {
+            const double span = ctl->eps_max - ctl->eps_min;
+            const double l = (ctl->eps_max - d.gap_lumo) / span, h = (ctl->eps_max - d.gap_homo) / span;
+            if (span > 0.0 && l < h) {
+                xl = (float)fmin(fmax(l, 0.0), 1.0);
+                xh = (float)fmin(fmax(h, 0.0), 1.0);
+            }
+        }
+        rc.xl[i] = xl;
+        rc.xh[i] = xh;
     }
     rc.chist[0] = SP2_CHOICE_INPUT;
+    rc.chist_a[0] = 1.0f;
 }
 
 // All threads of a CTA: sum, for every instance still running, the per-tile
@@ -263,10 +282,13 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const doub
             // component of the product error.  It is removed as the offset c_n of
             // X_n (sign of the layer: X^2 keeps it, 2X - X^2 negates it).  Both
             // sums are zero on the FP32 path, where c_n stays 0.
+            // An accelerated layer multiplies the product by +-a^2 (X^2: +, 2X - X^2: -).
             double c = 0.0;
+            const float a_made = (n == 0) ? 1.0f : rc.alpha[i];
             if (n > 0) {
                 const double gam = (rc.wprev[i] - ps) / (double)d.n;
-                c = (made == SP2_CHOICE_SQUARE) ? gam : -gam;
+                const double a2 = (double)a_made * (double)a_made;
+                c = (made == SP2_CHOICE_SQUARE) ? a2 * gam : -a2 * gam;
             }
             const double t = ts + (double)d.n * c;
             const double q = qs + 2.0 * c * ts + (double)d.n * c * c;
@@ -280,9 +302,11 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const doub
                 st.idem = t - q;
                 st.choice = made;
                 st.reserved = 0;
+                st.alpha = (double)a_made;
                 ctl->stat[n] = st;
             }
             rc.chist[n] = (signed char)made;
+            rc.chist_a[n] = a_made;
             const double e = fabs(t - q);
             const double e2 = rc.ehist[i][n & 1];
             rc.ehist[i][n & 1] = e;
@@ -346,6 +370,24 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const doub
             } else {
                 const int c = (d.nforced >= 0) ? d.forced[n] : layer_rule(t, q, d.n_occ);
                 rc.choice[i] = (signed char)c;
+                // Expansion of the accelerated layer: the tracked ends of the interval
+                // are balanced around the branch's fixed point, then follow the layer.
+                float a = 1.0f;
+                if (d.nforced >= 0 && d.forced_alpha) {
+                    a = (float)d.forced_alpha[n];
+                } else if (d.accel) {
+                    a = (c == SP2_CHOICE_SQUARE) ? 2.0f / (2.0f - rc.xl[i]) : 2.0f / (1.0f + rc.xh[i]);
+                    if (c == SP2_CHOICE_SQUARE) {
+                        const float tl = fmaf(a, rc.xl[i], 1.0f - a), th = fmaf(a, rc.xh[i], 1.0f - a);
+                        rc.xl[i] = tl * tl;
+                        rc.xh[i] = th * th;
+                    } else {
+                        const float tl = a * rc.xl[i], th = a * rc.xh[i];
+                        rc.xl[i] = fmaf(-tl, tl, 2.0f * tl);
+                        rc.xh[i] = fmaf(-th, th, 2.0f * th);
+                    }
+                }
+                rc.alpha[i] = a;
                 rc.ran[i] = 1;
                 rc.jobs[i] = (p.mode == MODE_RESPONSE) ? 2 : 1;
                 width = rc.jobs[i] * d.ntiles;

@@ -314,6 +314,7 @@ sp2_status run_fp64(const double *H_in, const double *Z_in, int N, double n_occ,
             ls.idem = rec[4 * l + 2];
             ls.choice = layer_rule(rec[4 * (l - 1) + 0], rec[4 * (l - 1) + 1], n_occ);
             ls.reserved = 0;
+            ls.alpha = 1.0;
             st->layer[L + l] = ls;
         }
         st->layers = L + refine_layers;

@@ -1,9 +1,10 @@
 // simt_kernel.cu -- the FP32 CUDA-core SP2 chain (the plain-precision comparator).
 //
 // One cooperative persistent launch runs every layer: per round each CTA takes
-// upper-triangle 128 x 128 tiles (bi <= bj) of X_{n+1} = X_n^2 or 2 X_n - X_n^2,
-// computes the tile with FP32 FMAs (the B operand is rows of X because X is
-// symmetric), writes the tile and its mirror, and records FP64 partials of
+// upper-triangle 128 x 128 tiles (bi <= bj) of X_{n+1} = X_n^2 or 2 X_n - X_n^2
+// (or the accelerated layer), computes the tile's product with FP32 FMAs on the
+// centred operand X - I/2 (the B operand is rows of X because X is symmetric),
+// writes the tile and its mirror, and records FP64 partials of
 // Tr X_{n+1} and ||X_{n+1}||_F^2.  A grid barrier ends the round; every CTA then
 // takes the same layer decision from the same partials (no host round trip).
 #include "device_common.cuh"
@@ -21,8 +22,11 @@ struct SimtSmem {
     double red[SIMT_THREADS / 32][2];
 };
 
-__device__ __forceinline__ void simt_tile_mma(const float *__restrict__ X, int np, int r0, int c0, SimtSmem &sm,
-                                              float acc[8][8]) {
+// acc = Y^2 over the tile for the centred operand Y = X - I/2 (I on the n real
+// diagonal entries): Y has the eigenvalues of X shifted into [-1/2, 1/2], so the
+// FP32 sums run over smaller terms; the epilogue adds X - I/4 back.
+__device__ __forceinline__ void simt_tile_mma(const float *__restrict__ X, int np, int n, int r0, int c0,
+                                              SimtSmem &sm, float acc[8][8]) {
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int lrow = tid >> 1, lk = (tid & 1) * 8;
@@ -35,16 +39,18 @@ __device__ __forceinline__ void simt_tile_mma(const float *__restrict__ X, int n
 
     float4 ra0 = *(const float4 *)Ap, ra1 = *(const float4 *)(Ap + 4);
     float4 rb0 = *(const float4 *)Bp, rb1 = *(const float4 *)(Bp + 4);
-    auto stash = [&](int buf) {
+    auto stash = [&](int buf, int kt) {
         const float a[8] = {ra0.x, ra0.y, ra0.z, ra0.w, ra1.x, ra1.y, ra1.z, ra1.w};
         const float b[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
+        const int k0 = kt * BK + lk;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            sm.A[buf][lk + q][lrow] = a[q];
-            sm.B[buf][lk + q][lrow] = b[q];
+            const int k = k0 + q;
+            sm.A[buf][lk + q][lrow] = (k == r0 + lrow && k < n) ? a[q] - 0.5f : a[q];
+            sm.B[buf][lk + q][lrow] = (k == c0 + lrow && k < n) ? b[q] - 0.5f : b[q];
         }
     };
-    stash(0);
+    stash(0, 0);
     __syncthreads();
     const int nk = np / BK;
     for (int kt = 0; kt < nk; ++kt) {
@@ -69,15 +75,24 @@ __device__ __forceinline__ void simt_tile_mma(const float *__restrict__ X, int n
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
-        if (kt + 1 < nk) stash(buf ^ 1);
+        if (kt + 1 < nk) stash(buf ^ 1, kt + 1);
         __syncthreads();
     }
 }
 
 // SP2 update of one tile, mirror store and FP64 partials.
+// X_{n+1} = k2 X^2 + k1 X + k0 I (I on the n real diagonal entries): the plain
+// layer (1, 0, 0) or (-1, 2, 0); the accelerated one T^2 with T = aX + (1 - a) I,
+// (a^2, 2a(1 - a), (1 - a)^2), or 2T - T^2 with T = aX, (-a^2, 2a, 0).  With
+// X^2 = acc + X - I/4 (acc = Y^2 of the centred operands) this is
+// k2 acc + (k2 + k1) X + (k0 - k2/4) I.
 __device__ __forceinline__ void simt_tile_epilogue(const float *__restrict__ Xold, float *__restrict__ Xnew, int np,
-                                                   int r0, int c0, int flip, const float acc[8][8], FF &ft, FF &fq) {
+                                                   int n, int r0, int c0, int flip, float alpha,
+                                                   const float acc[8][8], FF &ft, FF &fq) {
     const int tid = threadIdx.x;
+    const float k2 = flip ? -alpha * alpha : alpha * alpha;
+    const float kx = alpha * (2.0f - alpha);
+    const float kd = flip ? 0.25f * alpha * alpha : (1.0f - alpha) * (1.0f - alpha) - 0.25f * alpha * alpha;
     const int tx = tid & 15, ty = tid >> 4;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -86,13 +101,13 @@ __device__ __forceinline__ void simt_tile_epilogue(const float *__restrict__ Xol
         for (int h = 0; h < 2; ++h) {
             const int cb = c0 + (h == 0 ? tx * 4 : 64 + tx * 4);
             float v[4];
-            float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (flip) xo = *(const float4 *)(Xold + (size_t)r * np + cb);
+            const float4 xo = *(const float4 *)(Xold + (size_t)r * np + cb);
             const float xov[4] = {xo.x, xo.y, xo.z, xo.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float s = acc[i][h * 4 + q];
-                v[q] = flip ? (2.0f * xov[q] - s) : s;
+                const bool dg = (r == cb + q) && (r < n);
+                v[q] = fmaf(k2, s, fmaf(kx, xov[q], dg ? kd : 0.0f));
             }
             const bool all_owned = (r <= cb);
             if (all_owned) {
@@ -149,9 +164,10 @@ __global__ void __launch_bounds__(SIMT_THREADS) k_simt_persistent(const __grid_c
             const float *X = d.xf[n & 1];
             float *Xn = d.xf[(n + 1) & 1];
             float acc[8][8];
-            simt_tile_mma(X, d.np, bt.x * SIMT_T, bt.y * SIMT_T, sm, acc);
+            simt_tile_mma(X, d.np, d.n, bt.x * SIMT_T, bt.y * SIMT_T, sm, acc);
             FF ft = {0.f, 0.f}, fq = {0.f, 0.f};
-            simt_tile_epilogue(X, Xn, d.np, bt.x * SIMT_T, bt.y * SIMT_T, rc.choice[i] == SP2_CHOICE_FLIP, acc, ft, fq);
+            simt_tile_epilogue(X, Xn, d.np, d.n, bt.x * SIMT_T, bt.y * SIMT_T, rc.choice[i] == SP2_CHOICE_FLIP,
+                               rc.alpha[i], acc, ft, fq);
             // Deterministic block reduction of the tile partials.
             double t = ff_value(ft), q = ff_value(fq);
             for (int o = 16; o > 0; o >>= 1) {

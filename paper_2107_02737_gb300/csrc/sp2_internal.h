@@ -55,6 +55,7 @@ struct __align__(16) Part {
 struct LayerStatDev {
     double trace, trace_sq, idem;
     int choice, reserved;
+    double alpha;
 };
 
 struct InstCtl {
@@ -75,6 +76,10 @@ struct InstDesc {
     double n_occ;
     int nforced, nslots_x;            // nforced < 0: decide on device; nslots_x: 2 or L+1
     const int *forced;                // replayed layer choices (device)
+    const double *forced_alpha;       // replayed expansions a_n (device), or null
+    int accel;                        // 1: accelerated chain from [gap_homo, gap_lumo]
+    int pad_accel;
+    double gap_homo, gap_lumo;
     float *xf[2];
     uint16_t *xop;                    // slot s, op k at xop + (s*3 + k) * np * np
     float *yf[2];

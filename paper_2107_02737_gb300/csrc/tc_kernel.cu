@@ -227,6 +227,7 @@ struct TileWork {
     int flip;            // layer choice is 2X - X^2
     int n;               // forward layer index of the input (square jobs)
     float cf;            // offset c of the input X: true X = stored X + c I
+    float alpha;         // expansion a of the layer (1 = plain)
 };
 
 __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams &p, int g) {
@@ -245,6 +246,7 @@ __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams
         w.flip = rc.chist[m + 1] == SP2_CHOICE_FLIP;
         w.n = m;
         w.cf = (float)rc.chist_c[m];
+        w.alpha = rc.chist_a[m + 1];
     } else {
         const int n = rc.layer[w.inst];
         w.resp = w.job;
@@ -253,6 +255,7 @@ __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams
         w.flip = rc.choice[w.inst] == SP2_CHOICE_FLIP;
         w.n = n;
         w.cf = (float)rc.coff[w.inst];
+        w.alpha = rc.alpha[w.inst];
     }
     return w;
 }
@@ -497,6 +500,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 const int r = rw0 + lane;
                 const int nreal = d.n;
                 const float cf = w.cf;
+                // Accelerated layer (a != 1) in terms of the product P of the stored
+                // centred operands Y = X - I/2 (true Y = Y + cI): with T = aY + (1 - a/2) I
+                // (X^2 branch) or T = aY + (a/2) I (2X - X^2 branch),
+                //   X_{n+1} = ka (P + 2cY) + kb (Y + cI) + kc I,
+                // ka = +-a^2, kb = a (2 - a), kc = (1 - a/2)^2 or a (1 - a/4); the
+                // response / adjoint stream takes ka P + (kb + 2c ka) X1.
+                const bool accel = (w.alpha != 1.0f);
+                const float al = w.alpha;
+                const float ka = w.flip ? -al * al : al * al;
+                const float kb = al * (2.0f - al);
+                const float kc = w.flip ? al * (1.0f - 0.25f * al) : (1.0f - 0.5f * al) * (1.0f - 0.5f * al);
+                const float kx1 = fmaf(2.0f * cf, ka, kb);
                 FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f}, fp = {0.f, 0.f};
                 if (ok && rw0 < np) {
 #pragma unroll 1
@@ -523,9 +538,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 // P = Y^2 for the stored operands Y = X - I/2; the true input is
                                 // X + cI, so X^2 = P + 2cY + cI + X - I/4 (c^2 is below FP32 here).
                                 const float yo = dg ? xo - 0.5f : xo;
-                                const float b = dg ? P - 0.25f : P;
-                                if (!w.flip) x = (b + fmaf(2.0f * cf, yo, dg ? cf : 0.0f)) + xo;  // X^2
-                                else x = xo - (b + fmaf(2.0f * cf, yo, dg ? -cf : 0.0f));        // 2X - X^2
+                                if (accel) {
+                                    x = fmaf(ka, fmaf(2.0f * cf, yo, P), fmaf(kb, dg ? yo + cf : yo, dg ? kc : 0.0f));
+                                } else {
+                                    const float b = dg ? P - 0.25f : P;
+                                    if (!w.flip) x = (b + fmaf(2.0f * cf, yo, dg ? cf : 0.0f)) + xo;  // X^2
+                                    else x = xo - (b + fmaf(2.0f * cf, yo, dg ? -cf : 0.0f));        // 2X - X^2
+                                }
+                            } else if (accel) {
+                                x = fmaf(kx1, xo, ka * P);
                             } else {
                                 // P = Y X1 + X1 Y; with X = Y + (1/2 + c) I the chain needs
                                 // X X1 + X1 X = P + (1 + 2c) X1.
@@ -653,6 +674,7 @@ const void *tc_kernel_ptr(int precision) {
 
 }  // namespace
 
+static_assert(SMEM_BYTES <= 232448, "dynamic shared memory above the 227 KB a CTA can hold");
 size_t tc_smem_bytes() { return SMEM_BYTES; }
 
 // Number of CTAs of a co-resident persistent grid for the given CTA group size

@@ -19,7 +19,13 @@ With ``fixed_bounds`` the driver uses one interval for the whole trajectory,
 sum), which contains the spectrum of every H_k (Weyl); the layer sequence then
 changes only where the trajectory forces it.
 
-    python -m paper_2107_02737_gb300.md --n 12288 --steps 200
+With ``accelerate`` every step after the first runs the accelerated chain from an
+estimated HOMO / LUMO interval taken from the previous step's layer statistics
+(``gap.estimate_gap``); the interval only has to overlap the new gap, which a
+slowly moving trajectory keeps.  A step whose accelerated chain does not settle,
+or ends more than 1/2 away from the occupation, is rerun with the plain chain.
+
+    python -m paper_2107_02737_gb300.md --n 12288 --steps 200 [--accelerate]
 """
 from __future__ import annotations
 
@@ -33,6 +39,7 @@ from typing import List, Optional
 import numpy as np
 import torch
 
+from . import gap as gap_mod
 from . import inputs
 from . import sp2
 
@@ -45,12 +52,15 @@ class StepRecord:
     band_energy: float        # Tr[D_k H_k], FP64 on the device
     dE_dk: float              # Tr[D_k dH_k/dk]
     trace_err: float          # Tr D_k - n_occ
-    ms: float                 # device time of the response solve
+    ms: float                 # device time of the response solve (both solves after a fallback)
+    accelerated: bool = False # the step used an estimated HOMO / LUMO interval
+    fallback: bool = False    # ... which failed, so the step was rerun with the plain chain
 
 
 class MDSequence:
     def __init__(self, H0: torch.Tensor, V: torch.Tensor, n_occ: int, omega: float = 0.05,
-                 precision: str = "fp16", tol: float = 1e-6, fixed_bounds: bool = False):
+                 precision: str = "fp16", tol: float = 1e-6, fixed_bounds: bool = False,
+                 accelerate: bool = False):
         if H0.dtype != torch.float64 or V.dtype != torch.float64 or not H0.is_cuda:
             raise TypeError("H0 and V must be float64 CUDA tensors")
         self.H0, self.V, self.n_occ = H0, V, int(n_occ)
@@ -62,6 +72,8 @@ class MDSequence:
             _, r0 = sp2.density(H0, self.n_occ, precision=precision, tol=tol)
             vinf = float(V.abs().sum(dim=1).max())
             self.bounds = (r0.eps_min - vinf, r0.eps_max + vinf)
+        self.accelerate = bool(accelerate)
+        self.gap = None  # (eps_homo, eps_lumo) estimated from the previous step
         self.records: List[StepRecord] = []
         self.D: Optional[torch.Tensor] = None
         self.D1: Optional[torch.Tensor] = None
@@ -75,14 +87,25 @@ class MDSequence:
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        D, D1, res = sp2.response(Hk, H1k, self.n_occ, tol=self.tol, precision=self.precision, bounds=self.bounds)
+        use_gap = self.gap if self.accelerate else None
+        D, D1, res = sp2.response(Hk, H1k, self.n_occ, tol=self.tol, precision=self.precision, bounds=self.bounds,
+                                  gap=use_gap)
+        fallback = use_gap is not None and (not res.converged or abs(res.trace_D - self.n_occ) > 0.5)
+        if fallback:
+            D, D1, res = sp2.response(Hk, H1k, self.n_occ, tol=self.tol, precision=self.precision,
+                                      bounds=self.bounds)
         e1.record(stream)
         torch.cuda.synchronize()
         dE = float((D.double() * H1k).sum())
         rec = StepRecord(k, res.layers, res.stop_reason, res.band_energy, dE, res.trace_D - self.n_occ,
-                         e0.elapsed_time(e1))
+                         e0.elapsed_time(e1), use_gap is not None, fallback)
         self.records.append(rec)
         self.D, self.D1 = D, D1
+        if self.accelerate and res.converged:
+            est = gap_mod.estimate_gap(res.trace, res.trace_sq, res.choices, res.alphas, self.n_occ,
+                                       res.eps_min, res.eps_max)
+            if est is not None:
+                self.gap = est
         return rec
 
     def run(self, steps: int, start: int = 0) -> List[StepRecord]:
@@ -114,12 +137,13 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--precision", default="fp16")
     ap.add_argument("--fixed-bounds", action="store_true")
+    ap.add_argument("--accelerate", action="store_true")
     a = ap.parse_args(argv)
     t0 = time.time()
     ham, V = trajectory_inputs(a.n)
     gen_s = time.time() - t0
     run = MDSequence(torch.tensor(ham.H, device="cuda"), torch.tensor(V, device="cuda"), ham.n_occ,
-                     precision=a.precision, fixed_bounds=a.fixed_bounds)
+                     precision=a.precision, fixed_bounds=a.fixed_bounds, accelerate=a.accelerate)
     recs = run.run(a.steps)
     ms = [r.ms for r in recs[1:]] or [recs[0].ms]
     layers = [r.layers for r in recs]
@@ -127,6 +151,7 @@ def main(argv=None) -> int:
     # forward square (2N^3) plus the response product X X1 (2N^3) per layer
     eff = float(np.mean(layers)) * 4.0 * float(a.n) ** 3 / (mean_ms * 1e-3) / 1e12
     out = {"n": a.n, "steps": a.steps, "precision": a.precision, "fixed_bounds": a.fixed_bounds,
+           "accelerate": a.accelerate, "fallbacks": sum(1 for r in recs if r.fallback),
            "ms_per_step": mean_ms, "effective_tflops": eff, "layers_min": min(layers), "layers_max": max(layers),
            "not_converged_steps": sum(1 for r in recs if r.stop_reason == sp2.STOP_MAX),
            "max_abs_trace_err": max(abs(r.trace_err) for r in recs), "drift": run.drift(),

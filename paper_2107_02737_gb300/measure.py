@@ -11,6 +11,8 @@
 * ``md``       — H_k = H_0 + sin(0.05 k) V through sp2_response (see md.py).
 * ``refined``  — the N = 8192 chain plus two FP64 refinement layers (cuBLAS FP64
   emulated on the tensor cores); reports the added time and the trace.
+* ``accel``    — the N = 8192 chain, plain and accelerated from the generator's exact
+  HOMO / LUMO (and from an interval four gaps wide around it); ms to D and layers.
 
 Device time with CUDA events around each call, after warm-up; inputs resident on
 the device.  These are reports, not the headline benchmark (bench.py).
@@ -87,9 +89,26 @@ def refined(steps, warmup, n=8192, layers=2):
             "chain_trace_err": r0.trace_D - ham.n_occ, "idem_fro": float(torch.linalg.norm(D @ D - D))}
 
 
+def accel(steps, warmup, n=8192, precision="fp16"):
+    ham = inputs.water_like_workload(n)
+    H = torch.tensor(ham.H, device="cuda")
+    homo, lumo = float(ham.eigvals[ham.n_occ - 1]), float(ham.eigvals[ham.n_occ])
+    w = lumo - homo
+    out = {"workload": f"accelerated N={n}", "precision": precision, "gap": w}
+    for name, gap in [("plain", None), ("exact", (homo, lumo)), ("wide", (homo - 1.5 * w, lumo + 1.5 * w))]:
+        ms, (D, res) = _time(lambda: sp2.density(H, ham.n_occ, precision=precision, gap=gap), steps, warmup)
+        Dd = D.double()
+        idem = float(torch.linalg.norm(Dd @ Dd - Dd))
+        out[name] = {"ms_to_D": ms, "layers": res.layers, "trace_err": res.trace_D - ham.n_occ,
+                     "idem_fro": idem, "effective_tflops": res.layers * 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
+    return out
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", choices=["batched", "response", "adjoint", "md", "refined"], required=True)
+    ap.add_argument("--workload", choices=["batched", "response", "adjoint", "md", "refined", "accel"],
+                    required=True)
+    ap.add_argument("--accelerate", action="store_true", help="md: reuse HOMO / LUMO estimates step to step")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--n", type=int, default=0)
@@ -102,8 +121,10 @@ def main(argv=None) -> int:
         out = adjoint(a.steps, a.warmup, a.n or 4096)
     elif a.workload == "refined":
         out = refined(a.steps, a.warmup, a.n or 8192)
+    elif a.workload == "accel":
+        out = accel(a.steps, a.warmup, a.n or 8192)
     else:
-        return md.main(["--n", str(a.n or 12288), "--steps", str(a.steps)])
+        return md.main(["--n", str(a.n or 12288), "--steps", str(a.steps)] + (["--accelerate"] if a.accelerate else []))
     print(json.dumps(out))
     return 0
 

@@ -30,7 +30,7 @@ MAX_LAYERS_LIMIT = 200
 
 class LayerStat(ctypes.Structure):
     _fields_ = [("trace", ctypes.c_double), ("trace_sq", ctypes.c_double), ("idem", ctypes.c_double),
-                ("choice", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("choice", ctypes.c_int), ("reserved", ctypes.c_int), ("alpha", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_layers", ctypes.c_int), ("timeout_ms", ctypes.c_double),
                 ("user_bounds", ctypes.c_int), ("test_hook", ctypes.c_int), ("eps_min", ctypes.c_double),
-                ("eps_max", ctypes.c_double), ("profile", ctypes.c_int), ("cta_group", ctypes.c_int)]
+                ("eps_max", ctypes.c_double), ("profile", ctypes.c_int), ("cta_group", ctypes.c_int),
+                ("accelerate", ctypes.c_int), ("eps_homo", ctypes.c_double), ("eps_lumo", ctypes.c_double)]
 
 
 EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
@@ -126,6 +127,7 @@ class Result:
     raw: Stats = dataclasses.field(repr=False, default=None)
     phase_ms: List[float] = dataclasses.field(default_factory=list)
     cta_group: int = 0
+    alphas: List[float] = dataclasses.field(default_factory=list)  # expansion a_n, n = 1..layers
 
     @property
     def converged(self) -> bool:
@@ -133,7 +135,9 @@ class Result:
 
 
 def make_opts(precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0,
-              bounds: Optional[Sequence[float]] = None, profile: bool = False, cta_group: int = 0) -> Opts:
+              bounds: Optional[Sequence[float]] = None, profile: bool = False, cta_group: int = 0,
+              gap: Optional[Sequence[float]] = None) -> Opts:
+    """Options record; ``gap = (eps_homo, eps_lumo)`` selects the accelerated chain."""
     o = Opts()
     load().sp2_default_opts(ctypes.byref(o))
     if precision not in PRECISIONS:
@@ -146,6 +150,9 @@ def make_opts(precision: str = "fp16", max_layers: int = 100, timeout_ms: float 
         o.eps_min, o.eps_max = float(bounds[0]), float(bounds[1])
     o.profile = 1 if profile else 0
     o.cta_group = int(cta_group)
+    if gap is not None:
+        o.accelerate = 1
+        o.eps_homo, o.eps_lumo = float(gap[0]), float(gap[1])
     return o
 
 
@@ -163,7 +170,7 @@ def _result(status: int, st: Stats) -> Result:
     lay = [st.layer[k] for k in range(n)]
     return Result(status, st.layers, st.stop_reason, st.eps_min, st.eps_max, st.band_energy, st.trace_D,
                   [l.trace for l in lay], [l.trace_sq for l in lay], [l.idem for l in lay],
-                  [l.choice for l in lay[1:]], st, list(st.phase_ms), st.cta_group)
+                  [l.choice for l in lay[1:]], st, list(st.phase_ms), st.cta_group, [l.alpha for l in lay[1:]])
 
 
 def _check(status: int, where: str):
@@ -210,16 +217,19 @@ def workspace_bytes(n: int, kind: str = "density", precision: str = "fp16", laye
 
 def density(H: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16", max_layers: int = 100,
             timeout_ms: float = 2000.0, bounds=None, out: Optional[torch.Tensor] = None,
-            workspace: Optional[torch.Tensor] = None, stream=None, profile: bool = False, cta_group: int = 0):
+            workspace: Optional[torch.Tensor] = None, stream=None, profile: bool = False, cta_group: int = 0,
+            gap: Optional[Sequence[float]] = None):
     """D = theta(mu I - H) by the DNN-SP2 chain; returns (D, Result).
 
     ``cta_group`` selects the tensor-core tile shape (0 = library's choice, 1 or 2).
+    ``gap = (eps_homo, eps_lumo)``: accelerated chain from an estimated interval that
+    overlaps the gap between the highest occupied and lowest unoccupied eigenvalue.
     """
     H = _f64(H, "H")
     n = _square(H, "H")
     D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms, bounds, profile, cta_group)
+    o = make_opts(precision, max_layers, timeout_ms, bounds, profile, cta_group, gap)
     ws, wsb = _ws_args(workspace)
     s = load().sp2_density(ctypes.c_void_p(H.data_ptr()), n, float(n_occ), float(tol), ctypes.c_void_p(D.data_ptr()),
                            ctypes.byref(st), ctypes.byref(o), ws, wsb, ctypes.c_void_p(_stream_handle(H, stream)))
@@ -229,14 +239,16 @@ def density(H: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp
 
 def response(H: torch.Tensor, H1: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16",
              max_layers: int = 100, timeout_ms: float = 2000.0, fwd: Optional[Result] = None,
-             workspace: Optional[torch.Tensor] = None, stream=None, bounds=None, cta_group: int = 0):
-    """First-order response of the chain; returns (D, D1, Result)."""
+             workspace: Optional[torch.Tensor] = None, stream=None, bounds=None, cta_group: int = 0,
+             gap: Optional[Sequence[float]] = None):
+    """First-order response of the chain; returns (D, D1, Result).  ``gap`` as for ``density``
+    (with ``fwd`` the forward run's layer signs and expansions are replayed instead)."""
     H, H1 = _f64(H, "H"), _f64(H1, "H1")
     n = _square(H, "H")
     D = torch.empty((n, n), dtype=torch.float32, device=H.device)
     D1 = torch.empty((n, n), dtype=torch.float32, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms, bounds, cta_group=cta_group)
+    o = make_opts(precision, max_layers, timeout_ms, bounds, cta_group=cta_group, gap=gap)
     ws, wsb = _ws_args(workspace)
     fp = ctypes.byref(fwd.raw) if fwd is not None else None
     s = load().sp2_response(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(H1.data_ptr()), n, float(n_occ),
@@ -248,14 +260,15 @@ def response(H: torch.Tensor, H1: torch.Tensor, n_occ: int, tol: float = 1e-6, p
 
 def adjoint(H: torch.Tensor, G: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16",
             max_layers: int = 100, timeout_ms: float = 2000.0, fwd: Optional[Result] = None,
-            workspace: Optional[torch.Tensor] = None, stream=None):
-    """Gradient dTr[D G]/dH of the chain by reverse accumulation; returns (D, dH, Result)."""
+            workspace: Optional[torch.Tensor] = None, stream=None, gap: Optional[Sequence[float]] = None):
+    """Gradient dTr[D G]/dH of the chain by reverse accumulation; returns (D, dH, Result).
+    ``gap`` as for ``density`` (with ``fwd`` its signs and expansions are replayed)."""
     H, G = _f64(H, "H"), _f64(G, "G")
     n = _square(H, "H")
     D = torch.empty((n, n), dtype=torch.float32, device=H.device)
     dH = torch.empty((n, n), dtype=torch.float32, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms)
+    o = make_opts(precision, max_layers, timeout_ms, gap=gap)
     ws, wsb = _ws_args(workspace)
     fp = ctypes.byref(fwd.raw) if fwd is not None else None
     s = load().sp2_adjoint(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(G.data_ptr()), n, float(n_occ),
@@ -335,13 +348,15 @@ def density_noalloc(H: torch.Tensor, n_occ: int, out: torch.Tensor, tol: float =
 
 
 def density_refined(H: torch.Tensor, n_occ: int, refine_layers: int = 2, tol: float = 1e-6,
-                    precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0, stream=None):
-    """The chain plus ``refine_layers`` FP64 layers; returns (D float64, Result)."""
+                    precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0, stream=None,
+                    gap: Optional[Sequence[float]] = None):
+    """The chain plus ``refine_layers`` FP64 layers; returns (D float64, Result).  ``gap`` as for
+    ``density`` (the FP64 layers are plain)."""
     H = _f64(H, "H")
     n = _square(H, "H")
     D = torch.empty((n, n), dtype=torch.float64, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms)
+    o = make_opts(precision, max_layers, timeout_ms, gap=gap)
     s = load().sp2_density_refined(ctypes.c_void_p(H.data_ptr()), n, float(n_occ), float(tol), int(refine_layers),
                                    ctypes.c_void_p(D.data_ptr()), ctypes.byref(st), ctypes.byref(o),
                                    ctypes.c_void_p(_stream_handle(H, stream)))

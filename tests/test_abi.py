@@ -68,6 +68,31 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
     o = sp2.make_opts(bounds=(1.0, 0.0))
     assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
+    # the accelerated chain needs an ordered, finite interval
+    for gap in [(0.5, 0.5), (0.6, 0.1), (float("nan"), 0.1), (0.0, float("inf"))]:
+        o = sp2.make_opts(gap=gap)
+        assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
+
+
+def test_acceleration_rejected_where_unsupported(lib):
+    o = sp2.make_opts(gap=(-0.1, 0.1))
+    H = np.eye(8)
+    D = np.zeros((8, 8), np.float32)
+    hp = (ctypes.c_void_p * 1)(H.ctypes.data)
+    dp = (ctypes.c_void_p * 1)(D.ctypes.data)
+    nn = (ctypes.c_int * 1)(8)
+    occ = (ctypes.c_double * 1)(4.0)
+    assert lib.sp2_density_batched(1, hp, nn, occ, 1e-6, dp, None, ctypes.byref(o), None, 0, None) == sp2.ERR_ARG
+    ch = (ctypes.c_int * 1)(0)
+    X = np.zeros((8, 8), np.float32)
+    assert lib.sp2_apply_layers(X.ctypes.data_as(ctypes.c_void_p), 8, ch, 1, X.ctypes.data_as(ctypes.c_void_p),
+                                None, ctypes.byref(o), None) == sp2.ERR_ARG
+
+
+def test_layer_stat_record_layout():
+    # sp2_layer_stat: three doubles, two ints, the expansion a_n
+    assert ctypes.sizeof(sp2.LayerStat) == 40 and sp2.LayerStat.alpha.offset == 32
+    assert sp2.Opts.eps_lumo.offset == ctypes.sizeof(sp2.Opts) - 8
 
 
 def test_apply_layers_rejects_bad_choices(lib):

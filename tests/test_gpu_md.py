@@ -23,10 +23,10 @@ def trajectory():
     return ham, V
 
 
-@pytest.mark.parametrize("fixed", [False, True])
-def test_md_steps_match_oracle(trajectory, fixed):
+@pytest.mark.parametrize("fixed,accelerate", [(False, False), (True, False), (False, True)])
+def test_md_steps_match_oracle(trajectory, fixed, accelerate):
     ham, V = trajectory
-    run = md.MDSequence(dev(ham.H), dev(V), ham.n_occ, omega=0.3, fixed_bounds=fixed)
+    run = md.MDSequence(dev(ham.H), dev(V), ham.n_occ, omega=0.3, fixed_bounds=fixed, accelerate=accelerate)
     E_ref, F_ref = [], []
     for k in range(10):
         rec = run.step(k)
@@ -45,6 +45,10 @@ def test_md_steps_match_oracle(trajectory, fixed):
         assert rec.dE_dk == pytest.approx(F_ref[-1], abs=1e-3 * max(1e-3, abs(F_ref[-1])))
     if fixed:
         assert len({r.layers for r in run.records}) <= 2   # one interval: near-constant chain length
+    if accelerate:
+        # steps after the first reuse the previous step's HOMO / LUMO estimate
+        assert all(r.accelerated for r in run.records[1:]) and not any(r.fallback for r in run.records)
+        assert max(r.layers for r in run.records[1:]) < run.records[0].layers
     dr = run.drift()
     E_ref, F_ref = np.array(E_ref), np.array(F_ref)
     integ = np.concatenate([[0.0], np.cumsum(0.5 * (F_ref[1:] + F_ref[:-1]))])
