@@ -224,6 +224,45 @@ sp2_status sp2_density_batched(int B, const double *const *H, const int *N, cons
                                void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Batch plans: the batched solve set up once and launched many times.
+ *
+ * Quantum-based MD rebuilds one density matrix per Hamiltonian at every time step
+ * (section "Microcanonical MD"), so a batch of snapshots or replicas of fixed sizes
+ * is solved over and over.  A plan fixes the instance sizes, occupations, device
+ * buffers (H[b] read, D[b] written), tolerance and options once, and owns its
+ * workspace.  sp2_batch_plan_launch then only enqueues device work on `stream`:
+ * a reset of the control blocks (device-to-device copy), a memset, and the same
+ * kernels as sp2_density_batched -- no allocation, no host copy, no host
+ * synchronisation.  A caller may therefore capture it in a CUDA graph and replay
+ * the graph after writing new Hamiltonians into the same H buffers.
+ *
+ * sp2_batch_plan_create: arguments as sp2_density_batched, but every H[b] and D[b]
+ * must be device memory (else SP2_ERR_ARG); sp2_opts.accelerate is rejected.
+ * With autotune = 1 and o->cta_group = 0 on a split precision, create times one
+ * solve with each tensor-core tile shape (CTA pairs, single CTAs) on these inputs
+ * and keeps the faster; the choice is cached per (precision, sizes) for the life
+ * of the process, so later plans of the same shape skip the timing.  Create runs
+ * (and synchronises) on `stream`; tuning writes D.  *plan receives the handle.
+ * sp2_batch_plan_launch: enqueue one solve of every instance on `stream`.
+ * sp2_batch_plan_stats: wait for the stream, then fill st[0..B-1] from the last
+ * launch (st may be NULL); returns the worst status as sp2_density_batched.
+ * sp2_batch_plan_cta_group: tile shape the plan uses (1, 2; 0 on the FP32 path).
+ * sp2_batch_plan_destroy: free the plan and its workspace (NULL is ignored); the
+ * caller must not destroy a plan with launches in flight.
+ * A plan is used by one host thread at a time; overlapping launches of the same
+ * plan on different streams share its workspace and race.
+ */
+typedef struct sp2_batch_plan sp2_batch_plan;
+
+sp2_status sp2_batch_plan_create(int B, const double *const *H, const int *N, const double *n_occ, double tol,
+                                 float *const *D, const sp2_opts *o, int autotune, void *stream,
+                                 sp2_batch_plan **plan);
+sp2_status sp2_batch_plan_launch(sp2_batch_plan *plan, void *stream);
+sp2_status sp2_batch_plan_stats(sp2_batch_plan *plan, sp2_stats *st, void *stream);
+int sp2_batch_plan_cta_group(const sp2_batch_plan *plan);
+void sp2_batch_plan_destroy(sp2_batch_plan *plan);
+
+/*
  * sp2_apply_layers -- apply a given layer sequence to a given X_0 (test and
  * tooling entry point: the matrix-square kernel without the input layer).
  *   X0       [in]  N x N FP32 symmetric start matrix.

@@ -10,7 +10,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "device_common.cuh"
@@ -763,7 +765,32 @@ size_t bytes_for(int mode, const std::vector<int> &ns, int layers, const sp2_opt
     return b1 > b2 ? b1 : b2;  // the tile shape is chosen per device at run time
 }
 
+// Tile shape chosen by timing, per (precision, sorted sizes); process-wide.
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, int>> g_tune;
+
+std::string tune_key(const Plan &pl) {
+    std::vector<int> ns;
+    for (auto &sp : pl.inst) ns.push_back(sp.n);
+    std::sort(ns.begin(), ns.end());
+    std::string k = std::to_string(pl.precision) + ":" + std::to_string(pl.mode);
+    for (int n : ns) k += "," + std::to_string(n);
+    return k;
+}
+
 }  // namespace
+
+struct sp2_batch_plan {
+    Prepared P;                        // non-trivial instances, in launch order
+    std::vector<int> order;            // P.pl.inst[i] is the caller's instance order[i]
+    std::vector<InstSpec> trivial;     // n_occ = 0 or N: D = 0 or I
+    std::vector<int> trivial_index;
+    int B = 0;
+    void *ws = nullptr;                // plan-owned workspace
+    ~sp2_batch_plan() {
+        if (ws) cudaFree(ws);
+    }
+};
 
 extern "C" {
 
@@ -806,6 +833,170 @@ size_t sp2_response_workspace_bytes(int N, const sp2_opts *o) { return bytes_for
 size_t sp2_adjoint_workspace_bytes(int N, int layers, const sp2_opts *o) {
     return bytes_for(MODE_ADJOINT, {N}, layers, o);
 }
+
+sp2_status sp2_batch_plan_create(int B, const double *const *H, const int *N, const double *n_occ, double tol,
+                                 float *const *D, const sp2_opts *opts, int autotune, void *stream,
+                                 sp2_batch_plan **plan) {
+    if (!plan) return SP2_ERR_ARG;
+    *plan = nullptr;
+    if (B < 1 || B > MAX_BATCH || !H || !N || !n_occ || !D || !(tol >= 0.0)) return SP2_ERR_ARG;
+    if (autotune < 0 || autotune > 1) return SP2_ERR_ARG;
+    const sp2_opts o = resolve_opts(opts);
+    sp2_status r = check_opts(o);
+    if (r != SP2_OK) return r;
+    if (o.accelerate || o.profile || o.test_hook) return SP2_ERR_ARG;
+    for (int b = 0; b < B; ++b) {
+        if (N[b] < 1 || N[b] > 65536 || !integral_occ(n_occ[b], N[b]) || !H[b] || !D[b]) return SP2_ERR_ARG;
+    }
+    for (int b = 0; b < B; ++b)
+        if (!is_device_ptr(H[b]) || !is_device_ptr(D[b])) return SP2_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::unique_ptr<sp2_batch_plan> pb(new sp2_batch_plan());
+    pb->B = B;
+    Plan pl;
+    pl.mode = MODE_DENSITY;
+    pl.precision = o.precision;
+    pl.path = (o.precision == SP2_FP32_SIMT) ? PATH_SIMT : PATH_TC;
+    std::vector<int> order;
+    for (int b = 0; b < B; ++b) {
+        InstSpec sp;
+        sp.n = N[b];
+        sp.n_occ = n_occ[b];
+        sp.H = H[b];
+        sp.D = D[b];
+        if (sp.n_occ == 0.0 || sp.n_occ == (double)sp.n) {
+            pb->trivial.push_back(sp);
+            pb->trivial_index.push_back(b);
+        } else {
+            order.push_back(b);
+        }
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return N[a] > N[c]; });
+    for (int b : order) {
+        InstSpec sp;
+        sp.n = N[b];
+        sp.n_occ = n_occ[b];
+        sp.H = H[b];
+        sp.D = D[b];
+        pl.inst.push_back(sp);
+        pl.slots.push_back(2);
+        pl.max_n = std::max(pl.max_n, sp.n);
+        pl.max_np = std::max(pl.max_np, round_up(sp.n, PAD));
+    }
+    pb->order = order;
+    if (!pl.inst.empty()) {
+        // Workspace for either tile shape, owned by the plan.
+        const size_t need = bytes_for(MODE_DENSITY, [&] {
+            std::vector<int> ns;
+            for (auto &sp : pl.inst) ns.push_back(sp.n);
+            return ns;
+        }(), 0, &o);
+        if (cudaMalloc(&pb->ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return SP2_ERR_NOMEM;
+        }
+        Arena arena(s);  // unused: every matrix is device-resident
+        int want = o.cta_group;
+        if (pl.path == PATH_TC && want == 0) {
+            const std::string key = tune_key(pl);
+            {
+                std::lock_guard<std::mutex> g(g_tune_mu);
+                for (auto &kv : g_tune)
+                    if (kv.first == key) want = kv.second;
+            }
+            if (want == 0 && autotune) {
+                // Time one solve per tile shape on these inputs (after one warm-up).
+                float best = 0.0f;
+                int best_cg = 0;
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+                    if (e0) cudaEventDestroy(e0);
+                    cudaGetLastError();
+                    return SP2_ERR_CUDA;
+                }
+                for (int cg = 2; cg >= 1; --cg) {
+                    Prepared T;
+                    T.pl = pl;
+                    if (choose_launch(T.pl, cg, T.grid) != SP2_OK) continue;
+                    if (prepare(T, o, tol, pb->ws, need, s, arena, false) != SP2_OK) continue;
+                    if (enqueue(T, s, nullptr) != SP2_OK) continue;
+                    cudaEventRecord(e0, s);
+                    if (enqueue(T, s, nullptr) != SP2_OK) continue;
+                    cudaEventRecord(e1, s);
+                    if (status_rank(collect(T, s, nullptr)) > 1) continue;  // an error, not a slow chain
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (best_cg == 0 || ms < best) {
+                        best = ms;
+                        best_cg = cg;
+                    }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                cudaGetLastError();
+                if (best_cg == 0) return SP2_ERR_UNSUPPORTED;
+                want = best_cg;
+                std::lock_guard<std::mutex> g(g_tune_mu);
+                g_tune.push_back({key, best_cg});
+            }
+        }
+        pb->P.pl = pl;
+        r = choose_launch(pb->P.pl, want, pb->P.grid);
+        if (r != SP2_OK) return r;
+        r = prepare(pb->P, o, tol, pb->ws, need, s, arena, false);
+        if (r != SP2_OK) return r;
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return SP2_ERR_CUDA;
+        }
+    } else {
+        pb->P.pl = pl;
+        pb->P.o = o;
+    }
+    *plan = pb.release();
+    return SP2_OK;
+}
+
+sp2_status sp2_batch_plan_launch(sp2_batch_plan *plan, void *stream) {
+    if (!plan) return SP2_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto &sp : plan->trivial)
+        if (launch_fill_trivial(sp.D, sp.n, sp.n_occ == 0.0 ? 0.0f : 1.0f, s) != cudaSuccess) {
+            cudaGetLastError();
+            return SP2_ERR_CUDA;
+        }
+    if (plan->P.pl.inst.empty()) return SP2_OK;
+    return enqueue(plan->P, s, nullptr);
+}
+
+sp2_status sp2_batch_plan_stats(sp2_batch_plan *plan, sp2_stats *st, void *stream) {
+    if (!plan) return SP2_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    sp2_status worst = SP2_OK;
+    if (!plan->P.pl.inst.empty()) {
+        for (size_t i = 0; i < plan->P.pl.inst.size(); ++i)
+            plan->P.pl.inst[i].st = st ? &st[plan->order[i]] : nullptr;
+        worst = collect(plan->P, s, nullptr);
+    } else if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return SP2_ERR_CUDA;
+    }
+    for (size_t k = 0; k < plan->trivial.size(); ++k) {
+        InstSpec sp = plan->trivial[k];
+        sp.D = nullptr;  // already written by the launch
+        sp.st = st ? &st[plan->trivial_index[k]] : nullptr;
+        sp2_status t = run_trivial(sp, s);
+        if (status_rank(t) > status_rank(worst)) worst = t;
+    }
+    return worst;
+}
+
+int sp2_batch_plan_cta_group(const sp2_batch_plan *plan) {
+    if (!plan || plan->P.pl.path != PATH_TC || plan->P.pl.inst.empty()) return 0;
+    return plan->P.pl.cg;
+}
+
+void sp2_batch_plan_destroy(sp2_batch_plan *plan) { delete plan; }
 
 size_t sp2_density_batched_workspace_bytes(int B, const int *N, const sp2_opts *o) {
     if (B < 1 || !N) return 0;

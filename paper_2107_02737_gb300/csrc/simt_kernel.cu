@@ -203,7 +203,18 @@ int simt_blocks_per_sm() {
 
 cudaError_t launch_simt_persistent(const RunParams &p, int grid, cudaStream_t s) {
     void *args[] = {(void *)&p};
-    return cudaLaunchCooperativeKernel((const void *)k_simt_persistent, dim3(grid), dim3(SIMT_THREADS), args, 0, s);
+    // Cooperative launch in the attribute form (also capturable in a CUDA graph).
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(SIMT_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void *)k_simt_persistent, args);
 }
 
 }  // namespace sp2i

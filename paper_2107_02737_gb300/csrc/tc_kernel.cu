@@ -717,9 +717,21 @@ int tc_grid_size(int cta_group, int sm_count) {
 
 cudaError_t launch_tc_persistent(const RunParams &p, int cta_group, int grid, cudaStream_t s) {
     void *args[] = {(void *)&p};
-    if (cta_group == 1)
-        return cudaLaunchCooperativeKernel(tc_kernel_ptr<1>(p.precision), dim3(grid), dim3(TC_THREADS), args,
-                                           SMEM_BYTES, s);
+    if (cta_group == 1) {
+        // Cooperative launch (co-residency of the whole grid), through the
+        // attribute form so that it can also be captured in a CUDA graph.
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelExC(&cfg, tc_kernel_ptr<1>(p.precision), args);
+    }
     // CTA pairs: a cluster launch of exactly as many pairs as the device holds
     // at once (cudaOccupancyMaxActiveClusters, one CTA per SM), so on an idle GPU
     // every pair is resident for the grid barrier.  Without the cooperative

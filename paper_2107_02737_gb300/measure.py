@@ -56,9 +56,22 @@ def batched(steps, warmup, precision="bf16"):
     for h, H in zip(hams, Hs):
         t, _ = _time(lambda: sp2.density(H, h.n_occ, precision=precision), 1, 1)
         seq_ms += t
+    # The same batch as a reusable plan (tile shape by the autotuner), launched
+    # directly and as a replayed CUDA graph.
+    plan = sp2.BatchPlan(Hs, occ, precision=precision, autotune=True)
+    plan_ms, _ = _time(plan.launch, steps, warmup)
+    graph = plan.capture()
+    graph_ms, _ = _time(graph.replay, steps, warmup)
+    pres, pstatus = plan.stats()
+    plan_cg = plan.cta_group
+    same = all(torch.equal(a, b) for a, b in zip(Ds, plan.Ds)) if plan_cg == res[0].cta_group else None
+    plan.close()
     return {"workload": "batched 64 x N in {128..2048}", "precision": precision, "ms_per_step": ms,
             "effective_tflops": work / (ms * 1e-3) / 1e12, "sum_layers": sum(r.layers for r in res),
-            "one_by_one_ms": seq_ms, "max_idempotency_per_sqrtN": idem, "max_trace_err": tr, "status": status}
+            "one_by_one_ms": seq_ms, "max_idempotency_per_sqrtN": idem, "max_trace_err": tr, "status": status,
+            "plan": {"cta_group": plan_cg, "launch_ms": plan_ms, "graph_replay_ms": graph_ms,
+                     "effective_tflops_graph": work / (graph_ms * 1e-3) / 1e12, "status": pstatus,
+                     "equal_to_batched_call": same}}
 
 
 def response(steps, warmup, n=4096):

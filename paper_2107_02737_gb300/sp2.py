@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
 EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
            "sp2_response", "sp2_response_workspace_bytes", "sp2_adjoint", "sp2_adjoint_workspace_bytes",
            "sp2_density_batched", "sp2_density_batched_workspace_bytes", "sp2_apply_layers",
-           "sp2_density_noalloc", "sp2_density_refined", "sp2_density_nonorth"]
+           "sp2_density_noalloc", "sp2_density_refined", "sp2_density_nonorth", "sp2_batch_plan_create",
+           "sp2_batch_plan_launch", "sp2_batch_plan_stats", "sp2_batch_plan_cta_group", "sp2_batch_plan_destroy"]
 NOALLOC_MAX_N = 512
 
 _lib = None
@@ -101,6 +102,16 @@ def load() -> ctypes.CDLL:
     lib.sp2_density_refined.restype = c_i
     lib.sp2_density_nonorth.argtypes = [c_p, c_p, c_i, c_d, c_d, c_i, c_p, P(Stats), P(Opts), c_p]
     lib.sp2_density_nonorth.restype = c_i
+    lib.sp2_batch_plan_create.argtypes = [c_i, P(c_p), P(c_i), P(c_d), c_d, P(c_p), P(Opts), c_i, c_p, P(c_p)]
+    lib.sp2_batch_plan_create.restype = c_i
+    lib.sp2_batch_plan_launch.argtypes = [c_p, c_p]
+    lib.sp2_batch_plan_launch.restype = c_i
+    lib.sp2_batch_plan_stats.argtypes = [c_p, P(Stats), c_p]
+    lib.sp2_batch_plan_stats.restype = c_i
+    lib.sp2_batch_plan_cta_group.argtypes = [c_p]
+    lib.sp2_batch_plan_cta_group.restype = c_i
+    lib.sp2_batch_plan_destroy.argtypes = [c_p]
+    lib.sp2_batch_plan_destroy.restype = None
     _lib = lib
     return lib
 
@@ -309,6 +320,89 @@ def density_batched(Hs: Sequence[torch.Tensor], n_occs: Sequence[int], tol: floa
         r.status = ERR_NOT_CONVERGED if r.stop_reason == STOP_MAX else OK
         r._keep = keep  # the per-layer arrays behind r.raw
     return Ds, res, s
+
+
+class BatchPlan:
+    """A batched solve set up once (``sp2_batch_plan_create``) and launched many times.
+
+    ``Hs`` and ``outs`` (float32, default: allocated here) are device tensors that the
+    plan reads and writes on every launch; write new Hamiltonians into ``Hs`` in place
+    between launches.  ``launch`` only enqueues device work, so it can be captured in
+    a CUDA graph (``capture``).  ``autotune`` picks the tensor-core tile shape by
+    timing both on these inputs (cached per sizes for the process).
+    """
+
+    def __init__(self, Hs: Sequence[torch.Tensor], n_occs: Sequence[int], tol: float = 1e-6,
+                 precision: str = "bf16", max_layers: int = 100, timeout_ms: float = 2000.0,
+                 outs: Optional[Sequence[torch.Tensor]] = None, autotune: bool = True, cta_group: int = 0,
+                 stream=None):
+        self.B = len(Hs)
+        for i, h in enumerate(Hs):
+            if h.dtype != torch.float64 or not h.is_cuda or not h.is_contiguous():
+                raise TypeError(f"H[{i}] must be a contiguous float64 CUDA tensor")
+        self.Hs = list(Hs)
+        ns = [_square(h, f"H[{i}]") for i, h in enumerate(Hs)]
+        self.Ds = list(outs) if outs is not None else [torch.empty((n, n), dtype=torch.float32, device=h.device)
+                                                        for n, h in zip(ns, Hs)]
+        self.n_occs = [int(x) for x in n_occs]
+        hp = (ctypes.c_void_p * self.B)(*[h.data_ptr() for h in self.Hs])
+        dp = (ctypes.c_void_p * self.B)(*[d.data_ptr() for d in self.Ds])
+        nn = (ctypes.c_int * self.B)(*ns)
+        occ = (ctypes.c_double * self.B)(*[float(x) for x in n_occs])
+        o = make_opts(precision, max_layers, timeout_ms, cta_group=cta_group)
+        handle = ctypes.c_void_p()
+        self._lib = load()
+        s = self._lib.sp2_batch_plan_create(self.B, hp, nn, occ, float(tol), dp, ctypes.byref(o), 1 if autotune else 0,
+                                            ctypes.c_void_p(_stream_handle(self.Hs[0], stream)),
+                                            ctypes.byref(handle))
+        _check(s, "sp2_batch_plan_create")
+        self._h = handle
+
+    @property
+    def cta_group(self) -> int:
+        return int(self._lib.sp2_batch_plan_cta_group(self._h))
+
+    def launch(self, stream=None):
+        s = self._lib.sp2_batch_plan_launch(self._h, ctypes.c_void_p(_stream_handle(self.Hs[0], stream)))
+        _check(s, "sp2_batch_plan_launch")
+
+    def stats(self, stream=None):
+        """Wait for the stream; per-instance Results of the last launch and the worst status."""
+        sts = (Stats * self.B)()
+        keep = []
+        for b in range(self.B):
+            arr = (LayerStat * (MAX_LAYERS_LIMIT + 1))()
+            keep.append(arr)
+            sts[b].layer = ctypes.cast(arr, ctypes.POINTER(LayerStat))
+            sts[b].layer_cap = MAX_LAYERS_LIMIT + 1
+        s = self._lib.sp2_batch_plan_stats(self._h, sts, ctypes.c_void_p(_stream_handle(self.Hs[0], stream)))
+        _check(s, "sp2_batch_plan_stats")
+        res = [_result(OK, sts[b]) for b in range(self.B)]
+        for r in res:
+            r.status = ERR_NOT_CONVERGED if r.stop_reason == STOP_MAX else OK
+            r._keep = keep
+        return res, s
+
+    def capture(self):
+        """A torch CUDA graph holding one launch; ``graph.replay()`` re-runs the batch."""
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=self.Hs[0].device)
+        side.wait_stream(torch.cuda.current_stream(self.Hs[0].device))
+        with torch.cuda.graph(g, stream=side):
+            self.launch(stream=side)
+        torch.cuda.current_stream(self.Hs[0].device).wait_stream(side)
+        return g
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sp2_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def apply_layers(X0: torch.Tensor, choices: Sequence[int], precision: str = "fp16", timeout_ms: float = 2000.0,

@@ -108,3 +108,27 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(sp2, "_LIB_PATH", str(tmp_path / "libsp2.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         sp2.load()
+
+
+def test_batch_plan_rejects_bad_arguments_on_host(lib):
+    handle = ctypes.c_void_p()
+    H = np.eye(8)
+    D = np.zeros((8, 8), np.float32)
+    hp = (ctypes.c_void_p * 1)(H.ctypes.data)
+    dp = (ctypes.c_void_p * 1)(D.ctypes.data)
+    nn = (ctypes.c_int * 1)(8)
+    occ = (ctypes.c_double * 1)(4.0)
+    bad_occ = (ctypes.c_double * 1)(4.5)
+    assert lib.sp2_batch_plan_create(0, hp, nn, occ, 1e-6, dp, None, 0, None, ctypes.byref(handle)) == sp2.ERR_ARG
+    assert lib.sp2_batch_plan_create(1, hp, nn, occ, 1e-6, dp, None, 0, None, None) == sp2.ERR_ARG
+    assert lib.sp2_batch_plan_create(1, hp, nn, bad_occ, 1e-6, dp, None, 0, None, ctypes.byref(handle)) == sp2.ERR_ARG
+    assert lib.sp2_batch_plan_create(1, hp, nn, occ, 1e-6, dp, None, 2, None, ctypes.byref(handle)) == sp2.ERR_ARG
+    o = sp2.make_opts(gap=(-0.1, 0.1))
+    assert lib.sp2_batch_plan_create(1, hp, nn, occ, 1e-6, dp, ctypes.byref(o), 0, None,
+                                     ctypes.byref(handle)) == sp2.ERR_ARG
+    # host matrices are not accepted by a plan (its launches make no host copies)
+    assert lib.sp2_batch_plan_create(1, hp, nn, occ, 1e-6, dp, None, 0, None, ctypes.byref(handle)) == sp2.ERR_ARG
+    assert not handle.value
+    assert lib.sp2_batch_plan_launch(None, None) == sp2.ERR_ARG
+    assert lib.sp2_batch_plan_cta_group(None) == 0
+    lib.sp2_batch_plan_destroy(None)
