@@ -143,6 +143,16 @@ typedef struct {
                              and adjoint replay the forward run's a_n from its stats. */
     double eps_homo;
     double eps_lumo;
+    int checkpoint_stride; /* sp2_adjoint only (ignored elsewhere): which forward layers keep their
+                             operands for the reverse sweep.  0 = every layer (default; 6 bytes per
+                             element per layer).  s >= 2 = every s-th layer X_0, X_s, X_2s, ...
+                             (operands and FP32 master, 10 bytes per element each) and a ring of
+                             s - 1 layers; the reverse sweep recomputes the layers between two kept
+                             ones from the earlier, with the forward's own signs, offsets and
+                             expansions, so the gradient is bit-identical to s = 0 at the cost of
+                             up to (s - 1)/s of the forward's squares again.  -1 = the s that needs
+                             the least memory for the chain's length.  A stride that would not
+                             save memory keeps every layer.  Range -1 .. SP2_MAX_LAYERS_LIMIT. */
 } sp2_opts;
 
 /* Fill `o` with the defaults. */
@@ -191,13 +201,16 @@ sp2_status sp2_response(const double *H, const double *H1, int N, double n_occ, 
                         const sp2_stats *fwd, float *D, float *D1, sp2_stats *st,
                         const sp2_opts *o, void *workspace, size_t ws_bytes, void *stream);
 
-/* Device bytes sp2_adjoint needs for a chain of `layers` layers. */
+/* Device bytes sp2_adjoint needs for a chain of `layers` layers (0 = o->max_layers),
+ * with o->checkpoint_stride taken into account. */
 size_t sp2_adjoint_workspace_bytes(int N, int layers, const sp2_opts *o);
 
 /*
  * sp2_adjoint -- gradient dTr[D G]/dH of the chain, by reverse accumulation.
- * Runs the forward chain storing every layer's split operands (replaying `fwd`
- * when given, else deciding as sp2_density), then G_L = (G + G^T)/2 and, for
+ * Runs the forward chain storing every layer's split operands, or every s-th
+ * with o->checkpoint_stride = s and the others recomputed during the reverse
+ * sweep (replaying `fwd` when given, else deciding as sp2_density; storage is
+ * sized for fwd->layers, else for o->max_layers), then G_L = (G + G^T)/2 and, for
  * the layer that made X_{n+1} from X_n, G_n = G_{n+1} X_n + X_n G_{n+1} (X^2)
  * or 2 G_{n+1} - (G_{n+1} X_n + X_n G_{n+1}) (2X - X^2), and returns
  * dH = -G_0/(eps_max - eps_min).  Layer signs and bounds are held constant.

@@ -176,8 +176,34 @@ struct Plan {
     int cg = 1;                       // CTAs per tensor-core tile
     std::vector<InstSpec> inst;       // non-trivial instances, in launch order
     std::vector<int> slots;           // nslots_x per instance
+    std::vector<int> ckpt_s, ckpt_k;  // adjoint checkpoint stride and kept layers (0: every layer kept)
     int max_np = 0, max_n = 0;
 };
+
+// Operand storage of an adjoint whose forward chain has at most `lmax` layers:
+// every X_n (lmax + 1 slots), or with checkpoint stride s the K = lmax/s + 1 kept
+// X_{ks} (slot + FP32 master each) plus a ring of s - 1 slots and two FP32
+// matrices for the recomputed layers.  stride -1 picks the s of least memory;
+// a stride that would not save memory keeps every layer.
+void adjoint_layout(int lmax, int stride, int &slots, int &s_out, int &k_out) {
+    slots = lmax + 1;
+    s_out = 0;
+    k_out = 0;
+    auto cost = [&](int s) {  // in units of np^2 bytes: 6 per slot, 4 per FP32 master
+        const int k = lmax / s + 1;
+        return 6 * (k + s - 1) + 4 * k + 8;
+    };
+    int s = stride;
+    if (stride < 0) {
+        s = 0;
+        for (int c = 2; c <= lmax; ++c)
+            if (s == 0 || cost(c) < cost(s)) s = c;
+    }
+    if (s < 2 || s > lmax || cost(s) >= 6 * (lmax + 1)) return;
+    s_out = s;
+    k_out = lmax / s + 1;
+    slots = k_out + s - 1;
+}
 
 size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr) {
     (void)offsets_unused;
@@ -205,6 +231,11 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
         if (pl.path == PATH_TC) {
             c.take((size_t)pl.slots[i] * 3 * mat * 2);
             c.take((size_t)pl.slots[i] * 3 * sizeof(CUtensorMap));
+            if (pl.ckpt_s[i] > 0) {
+                c.take((size_t)pl.ckpt_k[i] * mat * 4);
+                c.take(mat * 4);
+                c.take(mat * 4);
+            }
             if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
                 c.take(mat * 4);
                 c.take(mat * 4);
@@ -391,6 +422,13 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
                                        pl.precision))
                         return SP2_ERR_UNSUPPORTED;
                 }
+            if (pl.ckpt_s[i] > 0) {
+                d.ckpt_s = pl.ckpt_s[i];
+                d.ckpt_k = pl.ckpt_k[i];
+                d.ckf = (float *)c.take((size_t)d.ckpt_k * mat * 4);
+                d.rf[0] = (float *)c.take(mat * 4);
+                d.rf[1] = (float *)c.take(mat * 4);
+            }
             if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
                 d.yf[0] = (float *)c.take(mat * 4);
                 d.yf[1] = (float *)c.take(mat * 4);
@@ -651,6 +689,7 @@ sp2_status check_opts(const sp2_opts &o) {
     if (o.accelerate < 0 || o.accelerate > 1) return SP2_ERR_ARG;
     if (o.accelerate && !(std::isfinite(o.eps_homo) && std::isfinite(o.eps_lumo) && o.eps_homo < o.eps_lumo))
         return SP2_ERR_ARG;
+    if (o.checkpoint_stride < -1 || o.checkpoint_stride > SP2_MAX_LAYERS_LIMIT) return SP2_ERR_ARG;
     return SP2_OK;
 }
 
@@ -731,9 +770,12 @@ sp2_status run_instances(int mode, std::vector<InstSpec> &specs, double tol, con
     for (int k : order) {
         const InstSpec &sp = specs[k];
         pl.inst.push_back(sp);
-        int slots = 2;
-        if (mode == MODE_ADJOINT) slots = (sp.fwd ? sp.fwd->layers : o.max_layers) + 1;
+        int slots = 2, cs = 0, ck = 0;
+        if (mode == MODE_ADJOINT)
+            adjoint_layout(sp.fwd ? sp.fwd->layers : o.max_layers, o.checkpoint_stride, slots, cs, ck);
         pl.slots.push_back(slots);
+        pl.ckpt_s.push_back(cs);
+        pl.ckpt_k.push_back(ck);
         pl.max_n = std::max(pl.max_n, sp.n);
         pl.max_np = std::max(pl.max_np, round_up(sp.n, PAD));
     }
@@ -753,7 +795,11 @@ size_t bytes_for(int mode, const std::vector<int> &ns, int layers, const sp2_opt
         InstSpec sp;
         sp.n = n;
         pl.inst.push_back(sp);
-        pl.slots.push_back(mode == MODE_ADJOINT ? (layers > 0 ? layers : o.max_layers) + 1 : 2);
+        int slots = 2, cs = 0, ck = 0;
+        if (mode == MODE_ADJOINT) adjoint_layout(layers > 0 ? layers : o.max_layers, o.checkpoint_stride, slots, cs, ck);
+        pl.slots.push_back(slots);
+        pl.ckpt_s.push_back(cs);
+        pl.ckpt_k.push_back(ck);
         pl.max_n = std::max(pl.max_n, n);
         pl.max_np = std::max(pl.max_np, round_up(n, PAD));
     }
@@ -880,6 +926,8 @@ sp2_status sp2_batch_plan_create(int B, const double *const *H, const int *N, co
         sp.D = D[b];
         pl.inst.push_back(sp);
         pl.slots.push_back(2);
+        pl.ckpt_s.push_back(0);
+        pl.ckpt_k.push_back(0);
         pl.max_n = std::max(pl.max_n, sp.n);
         pl.max_np = std::max(pl.max_np, round_up(sp.n, PAD));
     }

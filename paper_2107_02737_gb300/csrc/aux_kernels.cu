@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
     const float inv_lo = (float)(inv - (double)inv_hi);
     const float inv_lo24 = inv_hi * 0x1p-24f;       // weight of the 2^24-scaled low part
     int bad_unused = 0;
-    float *__restrict__ xf = d.xf[0];
+    float *__restrict__ xf = xmaster(d, 0, false);
     uint16_t *__restrict__ op0 = d.xop;
     uint16_t *__restrict__ op1 = d.xop + (size_t)np * np;
     uint16_t *__restrict__ op2 = d.xop + 2 * (size_t)np * np;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mo
     if (blockIdx.x >= d.fin_blocks) return;
     const int n = d.n, np = d.np;
     const InstCtl *ctl = d.ctl;
-    const float *__restrict__ X = d.xf[ctl->final_x & 1];
+    const float *__restrict__ X = d.ckpt_s > 0 ? xmaster(d, ctl->layers, false) : d.xf[ctl->final_x & 1];
     const float *__restrict__ Y = d.yf[ctl->final_y & 1];
     const double *__restrict__ H = d.H;
     float *__restrict__ out = d.out;

@@ -137,6 +137,28 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int
 }
 
 // ---------------------------------------------------------------------------
+// Where X_n lives.  Without checkpointing: operand slot n mod nslots_x and FP32
+// master xf[n & 1].  With checkpoint stride s (adjoint): the kept X_{ks} in
+// operand slot k and FP32 master ckf[k]; every other X_n in slot K + (n mod s) - 1
+// and, while the forward chain runs, xf[n & 1] (so X_L stays there for the
+// output), while the reverse sweep recomputes it, rf[n & 1].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int xslot_of(const InstDesc &d, int n) {
+    if (d.ckpt_s > 0) {
+        const int r = n % d.ckpt_s;
+        return r == 0 ? n / d.ckpt_s : d.ckpt_k + r - 1;
+    }
+    return n % d.nslots_x;
+}
+__device__ __forceinline__ float *xmaster(const InstDesc &d, int n, bool recompute) {
+    if (d.ckpt_s > 0) {
+        if (n % d.ckpt_s == 0) return d.ckf + (size_t)(n / d.ckpt_s) * d.np * d.np;
+        return recompute ? d.rf[n & 1] : d.xf[n & 1];
+    }
+    return d.xf[n & 1];
+}
+
+// ---------------------------------------------------------------------------
 // Per-round control state kept in shared memory by every CTA.  Every CTA
 // computes the same decisions from the same FP64 partials in the same order,
 // so no broadcast between CTAs is needed; CTA 0 alone writes the statistics.
@@ -147,6 +169,9 @@ struct RoundCtl {
     int phase;                       // adjoint: 0 forward, 1 reverse
     int rev_left;                    // adjoint: reverse layers still to do
     int rev_total;                   // adjoint: forward layer count L
+    int rec_mode;                    // adjoint reverse round: 0 reverse layer, 1 recompute X_{rec_top + 1}
+    int rec_top;                     // adjoint checkpointing: highest n whose X_n is held for the segment
+    int rec_seg;                     // adjoint checkpointing: segment (m / s) of the layers held
     int prefix[MAX_BATCH + 1];       // active tile prefix over instances
     int layer[MAX_BATCH];            // index n of the current X_n
     int jobs[MAX_BATCH];             // 0 (inactive), 1 (square) or 2 (square + response)
@@ -173,6 +198,9 @@ __device__ __forceinline__ void round_ctl_init(RoundCtl &rc, const RunParams &p)
     rc.phase = 0;
     rc.rev_left = 0;
     rc.rev_total = 0;
+    rc.rec_mode = 0;
+    rc.rec_top = 0;
+    rc.rec_seg = 0;
     for (int i = 0; i < p.B; ++i) {
         InstCtl *ctl = p.inst[i].ctl;
         rc.layer[i] = 0;
@@ -251,18 +279,36 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const doub
         return;
     }
     if (rc.phase == 1) {  // adjoint reverse sweep (B == 1); layer[0] counts reverse rounds done
-        rc.layer[0] += 1;
-        rc.rev_left -= 1;
+        const InstDesc &d0 = p.inst[0];
+        if (rc.rec_mode) {
+            rc.rec_top += 1;  // X_{rec_top + 1} was recomputed
+        } else {
+            rc.layer[0] += 1;
+            rc.rev_left -= 1;
+        }
         rc.prefix[0] = 0;
         if (rc.rev_left <= 0) {
-            if (writer) p.inst[0].ctl->final_y = rc.layer[0] & 1;  // Y buffer holding G_0
+            if (writer) d0.ctl->final_y = rc.layer[0] & 1;  // Y buffer holding G_0
             rc.prefix[1] = 0;
             rc.total = 0;
             return;
         }
+        // The next reverse layer m needs X_m.  With checkpointing, entering a new
+        // segment leaves only its kept X_{seg s}; X_{seg s + 1} .. X_m are recomputed
+        // first, one round each, with the forward's own signs, offsets and expansions.
+        rc.rec_mode = 0;
+        if (d0.ckpt_s > 0) {
+            const int m = rc.rev_total - 1 - rc.layer[0];
+            const int seg = m / d0.ckpt_s;
+            if (seg != rc.rec_seg) {
+                rc.rec_seg = seg;
+                rc.rec_top = seg * d0.ckpt_s;
+            }
+            if (m > rc.rec_top) rc.rec_mode = 1;
+        }
         rc.jobs[0] = 1;
-        rc.prefix[1] = p.inst[0].ntiles;
-        rc.total = p.inst[0].ntiles;
+        rc.prefix[1] = d0.ntiles;
+        rc.total = d0.ntiles;
         return;
     }
     int acc = 0;
@@ -356,6 +402,10 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const doub
                     rc.rev_total = n;
                     rc.rev_left = n;
                     rc.layer[0] = 0;
+                    // The forward chain left X_{s floor((L-1)/s)} .. X_{L-1} in place.
+                    rc.rec_mode = 0;
+                    rc.rec_seg = (d.ckpt_s > 0 && n > 0) ? (n - 1) / d.ckpt_s : 0;
+                    rc.rec_top = n - 1;
                     rc.prefix[1] = 0;
                     rc.total = 0;
                     if (n == 0) {

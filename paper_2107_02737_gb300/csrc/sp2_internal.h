@@ -8,6 +8,10 @@
 //               B = [op1 | op2 | op1] (Eq. activ: A + B + B^T with the lo*lo term
 //               dropped, all three products in one FP32 accumulator).
 //   yf[2], yop  the response / adjoint stream (FP32 master + ops 1, 2).
+//   adjoint with checkpoint stride s: operand slots 0..K-1 hold X_0, X_s, ...,
+//               X_{(K-1)s} (with FP32 masters in ckf), slots K..K+s-2 the others
+//               by n mod s; the reverse sweep recomputes a segment's layers from
+//               its kept X into those slots (FP32 ping-pong rf).
 //   part[2]     FP64 partials per tile, ping-pong by layer parity: Tr X, ||X||_F^2,
 //               ||Y||_F^2 and Tr P (see Part).
 // Tensor-core path: the operands are the split of Y = X - I/2 (identity on the
@@ -74,7 +78,10 @@ struct InstDesc {
     int parts;                        // partial records per layer (tiles x CTAs per tile)
     int pad_parts;
     double n_occ;
-    int nforced, nslots_x;            // nforced < 0: decide on device; nslots_x: 2 or L+1
+    int nforced, nslots_x;            // nforced < 0: decide on device; nslots_x: 2, L+1 or K+s-1
+    int ckpt_s, ckpt_k;               // adjoint checkpointing: every s-th X kept (K of them), 0 = off
+    float *ckf;                       // FP32 masters of the kept X_{k s}, k < K (ckpt_s > 0)
+    float *rf[2];                     // FP32 ping-pong of X recomputed in the reverse sweep
     const int *forced;                // replayed layer choices (device)
     const double *forced_alpha;       // replayed expansions a_n (device), or null
     int accel;                        // 1: accelerated chain from [gap_homo, gap_lumo]

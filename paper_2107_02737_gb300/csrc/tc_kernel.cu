@@ -226,6 +226,7 @@ struct TileWork {
     int ybuf;            // Y input buffer (resp)
     int flip;            // layer choice is 2X - X^2
     int n;               // forward layer index of the input (square jobs)
+    int rec;             // square job recomputing a forward layer in the adjoint's reverse sweep
     float cf;            // offset c of the input X: true X = stored X + c I
     float alpha;         // expansion a of the layer (1 = plain)
 };
@@ -237,11 +238,22 @@ __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams
     const int2 bt = p.tiles[d.tile_off + w.tile];
     w.bi = bt.x;
     w.bj = bt.y;
-    if (rc.phase == 1) {  // adjoint reverse: G_m from G_{m+1} and X_m
+    w.rec = 0;
+    if (rc.phase == 1 && rc.rec_mode) {  // adjoint reverse, checkpointing: X_{n+1} again from X_n
+        const int n = rc.rec_top;
+        w.resp = 0;
+        w.rec = 1;
+        w.xslot = xslot_of(d, n);
+        w.ybuf = 0;
+        w.flip = rc.chist[n + 1] == SP2_CHOICE_FLIP;
+        w.n = n;
+        w.cf = (float)rc.chist_c[n];
+        w.alpha = rc.chist_a[n + 1];
+    } else if (rc.phase == 1) {  // adjoint reverse: G_m from G_{m+1} and X_m
         const int k = rc.layer[0];
         const int m = rc.rev_total - 1 - k;
         w.resp = 1;
-        w.xslot = m % d.nslots_x;
+        w.xslot = xslot_of(d, m);
         w.ybuf = k & 1;
         w.flip = rc.chist[m + 1] == SP2_CHOICE_FLIP;
         w.n = m;
@@ -250,7 +262,7 @@ __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams
     } else {
         const int n = rc.layer[w.inst];
         w.resp = w.job;
-        w.xslot = n % d.nslots_x;
+        w.xslot = xslot_of(d, n);
         w.ybuf = n & 1;
         w.flip = rc.choice[w.inst] == SP2_CHOICE_FLIP;
         w.n = n;
@@ -479,9 +491,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 uint16_t *__restrict__ o2;
                 bool write0;
                 if (!w.resp) {
-                    old = d.xf[w.n & 1];
-                    outf = d.xf[(w.n + 1) & 1];
-                    uint16_t *base = d.xop + (size_t)((w.n + 1) % d.nslots_x) * 3 * mat;
+                    old = xmaster(d, w.n, w.rec != 0);
+                    outf = xmaster(d, w.n + 1, w.rec != 0);
+                    uint16_t *base = d.xop + (size_t)xslot_of(d, w.n + 1) * 3 * mat;
                     o0 = base;
                     o1 = base + mat;
                     o2 = base + 2 * mat;

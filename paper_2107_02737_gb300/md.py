@@ -25,6 +25,11 @@ estimated HOMO / LUMO interval taken from the previous step's layer statistics
 slowly moving trajectory keeps.  A step whose accelerated chain does not settle,
 or ends more than 1/2 away from the occupation, is rerun with the plain chain.
 
+Every converged step also records the width of the HOMO / LUMO interval estimated
+from its own statistics (``gap.estimate_gap``; None when the chain gives none), and
+every ``check_gap_every``-th step the gap of H_k from a library eigenvalue solve, to
+flag a trajectory whose gap closes.
+
     python -m paper_2107_02737_gb300.md --n 12288 --steps 200 [--accelerate]
 """
 from __future__ import annotations
@@ -55,6 +60,8 @@ class StepRecord:
     ms: float                 # device time of the response solve (both solves after a fallback)
     accelerated: bool = False # the step used an estimated HOMO / LUMO interval
     fallback: bool = False    # ... which failed, so the step was rerun with the plain chain
+    gap_est: Optional[float] = None   # eps_lumo - eps_homo as estimated from the chain's statistics
+    gap_check: Optional[float] = None # HOMO-LUMO gap of H_k by a library eigenvalue solve (report only)
 
 
 class MDSequence:
@@ -82,7 +89,7 @@ class MDSequence:
         s, c = math.sin(self.omega * k), math.cos(self.omega * k)
         return self.H0 + s * self.V, (self.omega * c) * self.V
 
-    def step(self, k: int) -> StepRecord:
+    def step(self, k: int, check_gap: bool = False) -> StepRecord:
         Hk, H1k = self.hamiltonian(k)
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -101,16 +108,23 @@ class MDSequence:
                          e0.elapsed_time(e1), use_gap is not None, fallback)
         self.records.append(rec)
         self.D, self.D1 = D, D1
-        if self.accelerate and res.converged:
+        if res.converged:
             est = gap_mod.estimate_gap(res.trace, res.trace_sq, res.choices, res.alphas, self.n_occ,
                                        res.eps_min, res.eps_max)
             if est is not None:
-                self.gap = est
+                rec.gap_est = est[1] - est[0]
+                if self.accelerate:
+                    self.gap = est
+        if check_gap:
+            # Independent monitor of the trajectory's gap (the SP2 chain needs one):
+            # FP32 eigenvalues from cuSOLVER, far below the gap in error.  Not part of the path.
+            lam = torch.linalg.eigvalsh(Hk.float())
+            rec.gap_check = float(lam[self.n_occ] - lam[self.n_occ - 1])
         return rec
 
-    def run(self, steps: int, start: int = 0) -> List[StepRecord]:
+    def run(self, steps: int, start: int = 0, check_every: int = 0) -> List[StepRecord]:
         for k in range(start, start + steps):
-            self.step(k)
+            self.step(k, check_gap=check_every > 0 and (k - start) % check_every == 0)
         return self.records
 
     def drift(self) -> dict:
@@ -138,13 +152,15 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", default="fp16")
     ap.add_argument("--fixed-bounds", action="store_true")
     ap.add_argument("--accelerate", action="store_true")
+    ap.add_argument("--check-gap-every", type=int, default=20,
+                    help="eigenvalue check of the HOMO-LUMO gap every K steps (0 = off)")
     a = ap.parse_args(argv)
     t0 = time.time()
     ham, V = trajectory_inputs(a.n)
     gen_s = time.time() - t0
     run = MDSequence(torch.tensor(ham.H, device="cuda"), torch.tensor(V, device="cuda"), ham.n_occ,
                      precision=a.precision, fixed_bounds=a.fixed_bounds, accelerate=a.accelerate)
-    recs = run.run(a.steps)
+    recs = run.run(a.steps, check_every=a.check_gap_every)
     ms = [r.ms for r in recs[1:]] or [recs[0].ms]
     layers = [r.layers for r in recs]
     mean_ms = float(np.mean(ms))
@@ -155,6 +171,10 @@ def main(argv=None) -> int:
            "ms_per_step": mean_ms, "effective_tflops": eff, "layers_min": min(layers), "layers_max": max(layers),
            "not_converged_steps": sum(1 for r in recs if r.stop_reason == sp2.STOP_MAX),
            "max_abs_trace_err": max(abs(r.trace_err) for r in recs), "drift": run.drift(),
+           "min_gap_estimate": min((r.gap_est for r in recs if r.gap_est is not None), default=None),
+           "min_gap_checked": min((r.gap_check for r in recs if r.gap_check is not None), default=None),
+           "gap_checks": sum(1 for r in recs if r.gap_check is not None),
+           "steps_without_gap_estimate": sum(1 for r in recs if r.gap_est is None),
            "generation_s": gen_s}
     print(json.dumps(out))
     return 0

@@ -6,8 +6,9 @@
   grouped persistent launch per step; effective TFLOP/s = sum_i L_i 2 N_i^3 / t.
 * ``response`` — D and D1 at N = 4096 (water-like H, banded H1); counts 4 N^3 per
   layer (the square and the product X X1).
-* ``adjoint``  — dTr[DG]/dH at N = 4096, forward replayed from a density run;
-  counts 2 N^3 (forward) + 2 N^3 (reverse) per layer.
+* ``adjoint``  — dTr[DG]/dH at N = 4096, forward replayed from a density run, with
+  every layer kept and with checkpointed recomputation; counts 2 N^3 (forward) +
+  2 N^3 (reverse) per layer.
 * ``md``       — H_k = H_0 + sin(0.05 k) V through sp2_response (see md.py).
 * ``refined``  — the N = 8192 chain plus two FP64 refinement layers (cuBLAS FP64
   emulated on the tensor cores); reports the added time and the trace.
@@ -86,10 +87,20 @@ def adjoint(steps, warmup, n=4096):
     ham, _, G = inputs.differentiation_workload(n)
     H, Gd = torch.tensor(ham.H, device="cuda"), torch.tensor(G, device="cuda")
     _, fwd = sp2.density(H, ham.n_occ)
-    ms, (D, dH, res) = _time(lambda: sp2.adjoint(H, Gd, ham.n_occ, fwd=fwd), steps, warmup)
-    return {"workload": f"adjoint N={n}", "ms_per_step": ms, "layers": res.layers,
-            "effective_tflops": res.layers * 4.0 * n ** 3 / (ms * 1e-3) / 1e12,
-            "workspace_gb": sp2.workspace_bytes(n, "adjoint", layers=res.layers) / 1e9}
+    out = {"workload": f"adjoint N={n}"}
+    ref = None
+    # every layer kept, then the checkpoint stride of least memory (layers between kept
+    # ones recomputed in the reverse sweep; the gradient is the same bits)
+    for name, stride in [("stored", 0), ("checkpointed", -1)]:
+        ms, (D, dH, res) = _time(lambda: sp2.adjoint(H, Gd, ham.n_occ, fwd=fwd, checkpoint_stride=stride),
+                                 steps, warmup)
+        ref = dH if ref is None else ref
+        out[name] = {"ms_per_step": ms, "layers": res.layers,
+                     "effective_tflops": res.layers * 4.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                     "workspace_gb": sp2.workspace_bytes(n, "adjoint", layers=res.layers,
+                                                         checkpoint_stride=stride) / 1e9,
+                     "equal_to_stored": bool(torch.equal(dH, ref))}
+    return out
 
 
 def refined(steps, warmup, n=8192, layers=2):

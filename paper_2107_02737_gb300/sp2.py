@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_layers", ctypes.c_int), ("timeout_ms", ctypes.c_double),
                 ("user_bounds", ctypes.c_int), ("test_hook", ctypes.c_int), ("eps_min", ctypes.c_double),
                 ("eps_max", ctypes.c_double), ("profile", ctypes.c_int), ("cta_group", ctypes.c_int),
-                ("accelerate", ctypes.c_int), ("eps_homo", ctypes.c_double), ("eps_lumo", ctypes.c_double)]
+                ("accelerate", ctypes.c_int), ("eps_homo", ctypes.c_double), ("eps_lumo", ctypes.c_double),
+                ("checkpoint_stride", ctypes.c_int)]
 
 
 EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
@@ -147,8 +148,9 @@ class Result:
 
 def make_opts(precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0,
               bounds: Optional[Sequence[float]] = None, profile: bool = False, cta_group: int = 0,
-              gap: Optional[Sequence[float]] = None) -> Opts:
-    """Options record; ``gap = (eps_homo, eps_lumo)`` selects the accelerated chain."""
+              gap: Optional[Sequence[float]] = None, checkpoint_stride: int = 0) -> Opts:
+    """Options record; ``gap = (eps_homo, eps_lumo)`` selects the accelerated chain;
+    ``checkpoint_stride`` (adjoint only): 0 keeps every layer, s >= 2 every s-th, -1 picks s."""
     o = Opts()
     load().sp2_default_opts(ctypes.byref(o))
     if precision not in PRECISIONS:
@@ -164,6 +166,7 @@ def make_opts(precision: str = "fp16", max_layers: int = 100, timeout_ms: float 
     if gap is not None:
         o.accelerate = 1
         o.eps_homo, o.eps_lumo = float(gap[0]), float(gap[1])
+    o.checkpoint_stride = int(checkpoint_stride)
     return o
 
 
@@ -214,8 +217,9 @@ def _ws_args(workspace: Optional[torch.Tensor]):
     return ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
 
 
-def workspace_bytes(n: int, kind: str = "density", precision: str = "fp16", layers: int = 0) -> int:
-    o = make_opts(precision)
+def workspace_bytes(n: int, kind: str = "density", precision: str = "fp16", layers: int = 0,
+                    checkpoint_stride: int = 0) -> int:
+    o = make_opts(precision, checkpoint_stride=checkpoint_stride)
     lib = load()
     if kind == "density":
         return int(lib.sp2_density_workspace_bytes(n, ctypes.byref(o)))
@@ -271,15 +275,18 @@ def response(H: torch.Tensor, H1: torch.Tensor, n_occ: int, tol: float = 1e-6, p
 
 def adjoint(H: torch.Tensor, G: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp16",
             max_layers: int = 100, timeout_ms: float = 2000.0, fwd: Optional[Result] = None,
-            workspace: Optional[torch.Tensor] = None, stream=None, gap: Optional[Sequence[float]] = None):
+            workspace: Optional[torch.Tensor] = None, stream=None, gap: Optional[Sequence[float]] = None,
+            checkpoint_stride: int = 0):
     """Gradient dTr[D G]/dH of the chain by reverse accumulation; returns (D, dH, Result).
-    ``gap`` as for ``density`` (with ``fwd`` its signs and expansions are replayed)."""
+    ``gap`` as for ``density`` (with ``fwd`` its signs and expansions are replayed).
+    ``checkpoint_stride`` s >= 2 keeps every s-th layer and recomputes the rest in the
+    reverse sweep (same result bit for bit, less memory); -1 picks s."""
     H, G = _f64(H, "H"), _f64(G, "G")
     n = _square(H, "H")
     D = torch.empty((n, n), dtype=torch.float32, device=H.device)
     dH = torch.empty((n, n), dtype=torch.float32, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms, gap=gap)
+    o = make_opts(precision, max_layers, timeout_ms, gap=gap, checkpoint_stride=checkpoint_stride)
     ws, wsb = _ws_args(workspace)
     fp = ctypes.byref(fwd.raw) if fwd is not None else None
     s = load().sp2_adjoint(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(G.data_ptr()), n, float(n_occ),
@@ -483,19 +490,21 @@ class DensityMatrix(torch.autograd.Function):
     """D(H) by the SP2 chain with a reverse-mode gradient through the chain.
 
     backward(G) returns dTr[D G]/dH from ``sp2_adjoint`` replaying the forward's
-    layer signs and spectral bounds (both held constant).
+    layer signs and spectral bounds (both held constant); ``checkpoint_stride`` is
+    passed to it (recomputation of the layers between kept ones at large N).
     """
 
     @staticmethod
-    def forward(ctx, H, n_occ, tol=1e-6, precision="fp16", max_layers=100):
+    def forward(ctx, H, n_occ, tol=1e-6, precision="fp16", max_layers=100, checkpoint_stride=0):
         D, res = density(H, n_occ, tol=tol, precision=precision, max_layers=max_layers)
         ctx.save_for_backward(H)
         ctx.res, ctx.n_occ, ctx.tol, ctx.precision = res, n_occ, tol, precision
+        ctx.checkpoint_stride = checkpoint_stride
         return D
 
     @staticmethod
     def backward(ctx, grad_D):
         (H,) = ctx.saved_tensors
         _, dH, _ = adjoint(H, grad_D.to(torch.float64).contiguous(), ctx.n_occ, tol=ctx.tol,
-                           precision=ctx.precision, fwd=ctx.res)
-        return dH.to(H.dtype), None, None, None, None
+                           precision=ctx.precision, fwd=ctx.res, checkpoint_stride=ctx.checkpoint_stride)
+        return dH.to(H.dtype), None, None, None, None, None

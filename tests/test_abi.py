@@ -68,6 +68,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
     o = sp2.make_opts(bounds=(1.0, 0.0))
     assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
+    for stride in (-2, 201):
+        o = sp2.make_opts(checkpoint_stride=stride)
+        assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
     # the accelerated chain needs an ordered, finite interval
     for gap in [(0.5, 0.5), (0.6, 0.1), (float("nan"), 0.1), (0.0, float("inf"))]:
         o = sp2.make_opts(gap=gap)
@@ -92,7 +95,9 @@ def test_acceleration_rejected_where_unsupported(lib):
 def test_layer_stat_record_layout():
     # sp2_layer_stat: three doubles, two ints, the expansion a_n
     assert ctypes.sizeof(sp2.LayerStat) == 40 and sp2.LayerStat.alpha.offset == 32
-    assert sp2.Opts.eps_lumo.offset == ctypes.sizeof(sp2.Opts) - 8
+    # sp2_opts ends with eps_lumo and checkpoint_stride (padded to 8 bytes)
+    assert sp2.Opts.checkpoint_stride.offset == sp2.Opts.eps_lumo.offset + 8
+    assert ctypes.sizeof(sp2.Opts) == sp2.Opts.checkpoint_stride.offset + 8
 
 
 def test_apply_layers_rejects_bad_choices(lib):
@@ -132,3 +137,19 @@ def test_batch_plan_rejects_bad_arguments_on_host(lib):
     assert lib.sp2_batch_plan_launch(None, None) == sp2.ERR_ARG
     assert lib.sp2_batch_plan_cta_group(None) == 0
     lib.sp2_batch_plan_destroy(None)
+
+
+def test_adjoint_checkpoint_workspace(lib):
+    """Keeping every s-th layer (10 bytes per element each) plus a ring of s - 1 (6 bytes)
+    and two FP32 matrices instead of every layer (6 bytes per element each)."""
+    n, L = 1024, 35
+    mat = 1024 * 1024
+    full = sp2.workspace_bytes(n, "adjoint", layers=L)
+    for s in (2, 4, 6, 9):
+        k = L // s + 1
+        got = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=s)
+        assert full - got == pytest.approx(mat * (6 * (L + 1) - 6 * (k + s - 1) - 4 * k - 8), abs=1 << 20)
+    auto = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=-1)
+    assert auto == min(sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=s) for s in range(2, L + 1))
+    # a stride that saves nothing keeps every layer
+    assert sp2.workspace_bytes(n, "adjoint", layers=3, checkpoint_stride=2) == sp2.workspace_bytes(n, "adjoint", layers=3)

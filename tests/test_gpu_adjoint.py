@@ -79,3 +79,71 @@ def test_adjoint_zero_layers_and_trivial():
     assert np.allclose(host(dH), -0.5 * (G + G.T) / (hi - lo), atol=1e-6)
     _, dH0, r0 = sp2.adjoint(dev(H), dev(G), 0, precision="fp16")
     assert torch.count_nonzero(dH0) == 0 and r0.stop_reason == sp2.STOP_TRIVIAL
+
+
+# -- checkpointed recomputation: every s-th layer kept, the rest recomputed in the
+# reverse sweep from the forward's recorded signs, offsets and expansions --
+
+@pytest.fixture(scope="module")
+def stored_adjoints(case):
+    ham, G, _ = case
+    out = {}
+    for precision in ("fp16", "bf16"):
+        _, res = sp2.density(dev(ham.H), ham.n_occ, precision=precision)
+        out[precision] = (res,) + sp2.adjoint(dev(ham.H), dev(G), ham.n_occ, precision=precision)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+@pytest.mark.parametrize("stride", [2, 3, 4, 7, -1])
+@pytest.mark.parametrize("replay", [False, True])
+def test_checkpointed_adjoint_is_bit_identical(case, stored_adjoints, precision, stride, replay):
+    ham, G, _ = case
+    fwd, D0, dH0, r0 = stored_adjoints[precision]
+    D, dH, res = sp2.adjoint(dev(ham.H), dev(G), ham.n_occ, precision=precision,
+                             fwd=fwd if replay else None, checkpoint_stride=stride)
+    assert res.layers == r0.layers and res.choices == r0.choices
+    assert torch.equal(D, D0)
+    assert torch.equal(dH, dH0)
+
+
+def test_checkpointing_saves_workspace():
+    n, L = 4096, 33
+    full = sp2.workspace_bytes(n, "adjoint", layers=L)
+    auto = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=-1)
+    s6 = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=6)
+    assert auto <= s6 < full
+    assert auto < 0.6 * full
+
+
+def test_checkpointed_adjoint_accelerated(case):
+    ham, G, _ = case
+    gap = (float(ham.eigvals[ham.n_occ - 1]), float(ham.eigvals[ham.n_occ]))
+    D0, g0, r0 = sp2.adjoint(dev(ham.H), dev(G), ham.n_occ, precision="fp16", gap=gap)
+    assert any(a != 1.0 for a in r0.alphas)
+    D1, g1, r1 = sp2.adjoint(dev(ham.H), dev(G), ham.n_occ, precision="fp16", gap=gap, checkpoint_stride=3)
+    assert r1.alphas == r0.alphas
+    assert torch.equal(D1, D0) and torch.equal(g1, g0)
+    assert rel_err(host(g1), odens.adjoint(ham.H, G, ham.n_occ)) <= 3e-3
+
+
+def test_adjoint_differentiation_workload_4096_checkpointed():
+    """The differentiation workload (water-like H, N = 4096, symmetric Gaussian G) with the
+    stride of least memory: bit-identical to keeping every layer, and sampled rows of the
+    eigenbasis formula dTr[DG]/dH = C (C^T sym(G) C o F) C^T."""
+    ham, _, G = inputs.differentiation_workload(4096)
+    Ht, Gt = dev(ham.H), dev(G)
+    _, res = sp2.density(Ht, ham.n_occ, precision="fp16")
+    _, g0, _ = sp2.adjoint(Ht, Gt, ham.n_occ, precision="fp16", fwd=res)
+    D, g1, r1 = sp2.adjoint(Ht, Gt, ham.n_occ, precision="fp16", fwd=res, checkpoint_stride=-1)
+    assert r1.layers == res.layers
+    assert torch.equal(g1, g0)
+    C, lam = ham.eigvecs, ham.eigvals
+    F = odens.response_weights(lam, ham.n_occ)
+    M = (C.T @ odens.symmetrise(G) @ C) * F
+    pick = np.random.default_rng(2).choice(ham.n, size=6, replace=False)
+    ref = C[pick] @ M @ C.T
+    got = host(g1[torch.tensor(pick, device="cuda")])
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"\nN=4096 adjoint (checkpointed): layers={r1.layers} sampled-row rel err {err:.2e}")
+    assert err <= 1e-2

@@ -29,11 +29,17 @@ def test_md_steps_match_oracle(trajectory, fixed, accelerate):
     run = md.MDSequence(dev(ham.H), dev(V), ham.n_occ, omega=0.3, fixed_bounds=fixed, accelerate=accelerate)
     E_ref, F_ref = [], []
     for k in range(10):
-        rec = run.step(k)
+        rec = run.step(k, check_gap=(k % 3 == 0))
         Hk = ham.H + math.sin(0.3 * k) * V
         H1k = 0.3 * math.cos(0.3 * k) * V
         lam, C = odens.eigensystem(Hk)
-        assert odens.homo_lumo_gap(lam, ham.n_occ) > 0.02  # the trajectory keeps a gap
+        true_gap = odens.homo_lumo_gap(lam, ham.n_occ)
+        assert true_gap > 0.02  # the trajectory keeps a gap
+        # the chain's own estimate overlaps the gap, each end within half a gap of the true
+        # level; the eigenvalue check matches the oracle
+        assert rec.gap_est is not None and 0.0 < rec.gap_est <= 2.0 * true_gap
+        if rec.gap_check is not None:
+            assert rec.gap_check == pytest.approx(true_gap, abs=1e-4)
         D_ref = odens.density_from_eigensystem(C, ham.n_occ)
         D1_ref = odens.response_from_eigensystem(lam, C, H1k, ham.n_occ)
         assert rec.stop_reason in (sp2.STOP_TOL, sp2.STOP_STALL)
