@@ -116,7 +116,9 @@ typedef struct {
     double timeout_ms;    /* device wait limit, default 2000 */
     int user_bounds;      /* 0 = Gershgorin bounds (default), 1 = use eps_min / eps_max below */
     int test_hook;        /* 0 in normal use; 1 = CTA 0 withholds its first grid-barrier arrival, so
-                             the barrier wait must run out (tests the timeout path) */
+                             the barrier wait must run out (tests the timeout path); 2 = every
+                             device allocation the call makes reports failure (host-side
+                             injection; tests the SP2_ERR_NOMEM path) */
     double eps_min;
     double eps_max;
     int profile;          /* 1 = record per-phase device times into sp2_stats.phase_ms */
@@ -144,9 +146,9 @@ typedef struct {
     double eps_homo;
     double eps_lumo;
     int checkpoint_stride; /* sp2_adjoint only (ignored elsewhere): which forward layers keep their
-                             operands for the reverse sweep.  0 = every layer (default; 6 bytes per
+                             operands for the reverse sweep.  0 = every layer (default; 4 bytes per
                              element per layer).  s >= 2 = every s-th layer X_0, X_s, X_2s, ...
-                             (operands and FP32 master, 10 bytes per element each) and a ring of
+                             (operands and FP32 master, 8 bytes per element each) and a ring of
                              s - 1 layers; the reverse sweep recomputes the layers between two kept
                              ones from the earlier, with the forward's own signs, offsets and
                              expansions, so the gradient is bit-identical to s = 0 at the cost of
@@ -278,7 +280,10 @@ void sp2_batch_plan_destroy(sp2_batch_plan *plan);
 /*
  * sp2_apply_layers -- apply a given layer sequence to a given X_0 (test and
  * tooling entry point: the matrix-square kernel without the input layer).
- *   X0       [in]  N x N FP32 symmetric start matrix.
+ *   X0       [in]  N x N FP32 symmetric start matrix.  With SP2_FP16_SPLIT its entries
+ *                   must stay below 32 in magnitude (the split stores hi * 2^11 in FP16);
+ *                   a matrix with its spectrum in [0, 1], as every X_n of the chain, has
+ *                   entries of magnitude at most 1.
  *   choices  [in]  host array of n_layers SP2_CHOICE_SQUARE / SP2_CHOICE_FLIP.
  *   X        [out] N x N FP32 result X_{n_layers}.
  *   st       [out] per-layer traces (stop fields unused).

@@ -102,14 +102,18 @@ struct InstSpec {
     int nchoices = -1;
 };
 
-// Device allocation owned by one call; freed on every exit path.
+// Device allocation owned by one call; freed on every exit path.  With `fail`
+// set (sp2_opts.test_hook = 2, host-side fault injection) every allocation
+// reports failure, as an exhausted device would.
 struct Arena {
     std::vector<void *> ptrs;
     cudaStream_t s;
+    bool fail = false;
     explicit Arena(cudaStream_t st) : s(st) {}
     void *get(size_t bytes) {
         void *p = nullptr;
         if (bytes == 0) bytes = 256;
+        if (fail) return nullptr;
         if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
@@ -184,14 +188,15 @@ struct Plan {
 // every X_n (lmax + 1 slots), or with checkpoint stride s the K = lmax/s + 1 kept
 // X_{ks} (slot + FP32 master each) plus a ring of s - 1 slots and two FP32
 // matrices for the recomputed layers.  stride -1 picks the s of least memory;
-// a stride that would not save memory keeps every layer.
+// a stride that would not save memory keeps every layer.  A slot is two 16-bit
+// matrices (hi, lo), an FP32 master one 32-bit matrix: 4 bytes per element each.
 void adjoint_layout(int lmax, int stride, int &slots, int &s_out, int &k_out) {
     slots = lmax + 1;
     s_out = 0;
     k_out = 0;
-    auto cost = [&](int s) {  // in units of np^2 bytes: 6 per slot, 4 per FP32 master
+    auto cost = [&](int s) {  // in units of np^2 bytes: 4 per slot, 4 per FP32 master
         const int k = lmax / s + 1;
-        return 6 * (k + s - 1) + 4 * k + 8;
+        return 4 * (k + s - 1) + 4 * k + 8;
     };
     int s = stride;
     if (stride < 0) {
@@ -199,7 +204,7 @@ void adjoint_layout(int lmax, int stride, int &slots, int &s_out, int &k_out) {
         for (int c = 2; c <= lmax; ++c)
             if (s == 0 || cost(c) < cost(s)) s = c;
     }
-    if (s < 2 || s > lmax || cost(s) >= 6 * (lmax + 1)) return;
+    if (s < 2 || s > lmax || cost(s) >= 4 * (lmax + 1)) return;
     s_out = s;
     k_out = lmax / s + 1;
     slots = k_out + s - 1;
@@ -229,7 +234,7 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
         c.take(mat * 4);
         c.take(mat * 4);
         if (pl.path == PATH_TC) {
-            c.take((size_t)pl.slots[i] * 3 * mat * 2);
+            c.take((size_t)pl.slots[i] * 2 * mat * 2);
             c.take((size_t)pl.slots[i] * 3 * sizeof(CUtensorMap));
             if (pl.ckpt_s[i] > 0) {
                 c.take((size_t)pl.ckpt_k[i] * mat * 4);
@@ -239,7 +244,7 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
             if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
                 c.take(mat * 4);
                 c.take(mat * 4);
-                c.take(2 * 3 * mat * 2);
+                c.take(2 * 2 * mat * 2);
                 c.take(6 * sizeof(CUtensorMap));
             }
         }
@@ -410,18 +415,17 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         d.xf[0] = (float *)c.take(mat * 4);
         d.xf[1] = (float *)c.take(mat * 4);
         if (pl.path == PATH_TC) {
-            d.xop = (uint16_t *)c.take((size_t)d.nslots_x * 3 * mat * 2);
+            d.xop = (uint16_t *)c.take((size_t)d.nslots_x * 2 * mat * 2);
             d_xmaps[i] = (CUtensorMap *)c.take((size_t)d.nslots_x * 3 * sizeof(CUtensorMap));
             d.xmap = d_xmaps[i];
             h_xmaps[i].resize((size_t)d.nslots_x * 3);
+            // Three maps per slot for the K segments' operands op0, op1, op2 = hi, hi, lo
+            // over the slot's two matrices (hi, lo).
             for (int sl = 0; sl < d.nslots_x; ++sl)
-                for (int k = 0; k < 3; ++k) {
-                    // BF16 keeps op0 == op1: the map of op0 points at op1's matrix.
-                    const int src = (pl.precision == SP2_BF16_SPLIT && k == 0) ? 1 : k;
-                    if (!encode_op_map(&h_xmaps[i][sl * 3 + k], d.xop + ((size_t)sl * 3 + src) * mat, np,
+                for (int k = 0; k < 3; ++k)
+                    if (!encode_op_map(&h_xmaps[i][sl * 3 + k], d.xop + ((size_t)sl * 2 + (k == 2)) * mat, np,
                                        pl.precision))
                         return SP2_ERR_UNSUPPORTED;
-                }
             if (pl.ckpt_s[i] > 0) {
                 d.ckpt_s = pl.ckpt_s[i];
                 d.ckpt_k = pl.ckpt_k[i];
@@ -432,13 +436,13 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
             if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) {
                 d.yf[0] = (float *)c.take(mat * 4);
                 d.yf[1] = (float *)c.take(mat * 4);
-                d.yop = (uint16_t *)c.take(2 * 3 * mat * 2);
+                d.yop = (uint16_t *)c.take(2 * 2 * mat * 2);
                 d_ymaps[i] = (CUtensorMap *)c.take(6 * sizeof(CUtensorMap));
                 d.ymap = d_ymaps[i];
                 h_ymaps[i].resize(6);
                 for (int sl = 0; sl < 2; ++sl)
                     for (int k = 0; k < 3; ++k)
-                        if (!encode_op_map(&h_ymaps[i][sl * 3 + k], d.yop + ((size_t)sl * 3 + k) * mat, np,
+                        if (!encode_op_map(&h_ymaps[i][sl * 3 + k], d.yop + ((size_t)sl * 2 + (k == 2)) * mat, np,
                                            pl.precision))
                             return SP2_ERR_UNSUPPORTED;
             }
@@ -595,7 +599,7 @@ sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
     rp.mode = pl.mode;
     rp.precision = pl.precision;
     rp.max_layers = P.o.max_layers;
-    rp.test_hook = P.o.test_hook;
+    rp.test_hook = P.o.test_hook == 1 ? 1 : 0;  // the device sees only the barrier hook
     if (ev) CK(cudaEventRecord(ev[1], s));
     CK(pl.path == PATH_TC ? launch_tc_persistent(rp, pl.cg, P.grid, s) : launch_simt_persistent(rp, P.grid, s));
     if (ev) CK(cudaEventRecord(ev[2], s));
@@ -638,6 +642,7 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     sp2_status r = choose_launch(P.pl, o.cta_group, P.grid);
     if (r != SP2_OK) return r;
     Arena arena(s);
+    arena.fail = (o.test_hook == 2);
     const size_t need = plan_bytes(P.pl);
     if (ws && ws_bytes < need) return SP2_ERR_ARG;
     if (ws && ((uintptr_t)ws & 255)) return SP2_ERR_ARG;
@@ -683,7 +688,7 @@ sp2_status check_opts(const sp2_opts &o) {
     if (o.max_layers < 1 || o.max_layers > SP2_MAX_LAYERS_LIMIT) return SP2_ERR_ARG;
     if (!(o.timeout_ms > 0.0)) return SP2_ERR_ARG;
     if (o.user_bounds && !(o.eps_max > o.eps_min)) return SP2_ERR_ARG;
-    if (o.test_hook < 0 || o.test_hook > 1) return SP2_ERR_ARG;
+    if (o.test_hook < 0 || o.test_hook > 2) return SP2_ERR_ARG;
     if (o.profile < 0 || o.profile > 1) return SP2_ERR_ARG;
     if (o.cta_group < 0 || o.cta_group > 2) return SP2_ERR_ARG;
     if (o.accelerate < 0 || o.accelerate > 1) return SP2_ERR_ARG;

@@ -197,9 +197,8 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
     const float inv_lo24 = inv_hi * 0x1p-24f;       // weight of the 2^24-scaled low part
     int bad_unused = 0;
     float *__restrict__ xf = xmaster(d, 0, false);
-    uint16_t *__restrict__ op0 = d.xop;
-    uint16_t *__restrict__ op1 = d.xop + (size_t)np * np;
-    uint16_t *__restrict__ op2 = d.xop + 2 * (size_t)np * np;
+    uint16_t *__restrict__ op1 = d.xop;                    // hi
+    uint16_t *__restrict__ op2 = d.xop + (size_t)np * np;  // lo
     FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
     // Rows are strided over blocks, four consecutive columns per thread: no
     // index divisions on the hot loop; restrict-qualified so that the loads of
@@ -232,10 +231,9 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
             *(float4 *)(xf + idx) = make_float4(x[0], x[1], x[2], x[3]);
             if (PATH == PATH_TC) {
                 // operands of the first square: the split of Y_0 = X_0 - I/2
-                uint16_t a[4], b[4], c[4];
+                uint16_t b[4], c[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) split3<PREC>(y[q], a[q], b[q], c[q]);
-                if (PREC == SP2_FP16_SPLIT) *(ushort4 *)(op0 + idx) = make_ushort4(a[0], a[1], a[2], a[3]);
+                for (int q = 0; q < 4; ++q) split2<PREC, X_SHIFT>(y[q], b[q], c[q]);
                 *(ushort4 *)(op1 + idx) = make_ushort4(b[0], b[1], b[2], b[3]);
                 *(ushort4 *)(op2 + idx) = make_ushort4(c[0], c[1], c[2], c[3]);
             }
@@ -265,7 +263,7 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x_from(InstDesc *inst, con
     const InstDesc &d = inst[0];
     const int n = d.n, np = d.np;
     float *xf = d.xf[0];
-    uint16_t *op0 = d.xop, *op1 = d.xop + (size_t)np * np, *op2 = d.xop + 2 * (size_t)np * np;
+    uint16_t *op1 = d.xop, *op2 = d.xop + (size_t)np * np;
     FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
     for (int i = blockIdx.x; i < np; i += gridDim.x) {
         for (int j = threadIdx.x; j < np; j += AUX_THREADS) {
@@ -277,9 +275,8 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x_from(InstDesc *inst, con
             if (PATH == PATH_TC) {
                 const float y = (i == j && i < n) ? v - 0.5f : v;
                 ff_add_sq(fw, y, 1.0f);
-                uint16_t a, b, c;
-                split3<PREC>(y, a, b, c);
-                if (PREC == SP2_FP16_SPLIT) op0[idx] = a;
+                uint16_t b, c;
+                split2<PREC, X_SHIFT>(y, b, c);
                 op1[idx] = b;
                 op2[idx] = c;
             }
@@ -312,7 +309,7 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode
     if (mabs > 0.0 && isfinite(mabs)) frexp(mabs, &ex);  // mabs in [2^(ex-1), 2^ex)
     const double yscale = ldexp(1.0, -ex);
     const double c = coef * yscale;
-    uint16_t *op1 = d.yop + (size_t)np * np, *op2 = d.yop + 2 * (size_t)np * np;
+    uint16_t *op1 = d.yop, *op2 = d.yop + (size_t)np * np;
     for (int i = blockIdx.x; i < np; i += gridDim.x)
         for (int j = threadIdx.x; j < np; j += AUX_THREADS) {
         const size_t idx = (size_t)i * np + j;
@@ -323,8 +320,8 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode
         }
         const float y = (float)(0.5 * (a + b) * c);
         d.yf[0][idx] = y;
-        uint16_t o0, o1, o2;
-        split3<PREC>(y, o0, o1, o2);
+        uint16_t o1, o2;
+        split2<PREC, Y_SHIFT>(y, o1, o2);
         op1[idx] = o1;
         op2[idx] = o2;
     }

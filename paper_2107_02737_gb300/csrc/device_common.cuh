@@ -68,35 +68,41 @@ __host__ __device__ __forceinline__ double dkey_value(unsigned long long k) {
 
 // ---------------------------------------------------------------------------
 // The split X = X^(0) + X^(1) (section "Deep-neural network electronic structure
-// solver", the dual matrix representation), with round-to-nearest-even.
-// FP16: op1 = hi = FP16[x]; op2 = FP16[(x - hi) * 2^11]; op0 = hi * 2^11 (exact).
-//   lo is kept scaled so that it stays in FP16's normal range; every product in
-//   the K-loop then carries the same factor 2^11, removed in the epilogue.
-// BF16: op1 = op0 = hi = BF16[x]; op2 = BF16[x - hi] (no range problem).
-// x - hi is exact in FP32 in both cases.
+// solver", the dual matrix representation), with round-to-nearest-even, and
+// both parts stored times 2^SHIFT (exact power-of-two scaling):
+//   hi = FP16[x],  stored FP16[hi * 2^SHIFT],  lo = FP16[(x - hi) * 2^SHIFT].
+// x - hi is exact in FP32.  The X stream uses SHIFT = 11: lo ~ 2^-11 |x| then stays
+// in FP16's normal range, hi * 2^11 <= 2^11 cannot overflow (|x| <= 1), and all
+// three products of the square carry 2^22, removed in the epilogue.  The second
+// stream (response / adjoint), whose entries grow along the chain, keeps SHIFT = 0
+// (the full FP16 range for hi; a subnormal lo costs at most 2^-24 absolute).
+// BF16 needs no scaling (its exponent range is FP32's): SHIFT is ignored.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split_fp16(float x, uint16_t &o0, uint16_t &o1, uint16_t &o2) {
+constexpr int X_SHIFT = LO_SHIFT;   // X stream
+constexpr int Y_SHIFT = 0;          // response / adjoint stream
+
+template <int SHIFT>
+__device__ __forceinline__ void split_fp16(float x, uint16_t &hi, uint16_t &lo) {
     __half h = __float2half_rn(x);
-    float hf = __half2float(h);
-    o1 = __half_as_ushort(h);
-    o0 = __half_as_ushort(__float2half_rn(hf * (float)(1 << LO_SHIFT)));
-    o2 = __half_as_ushort(__float2half_rn(__fsub_rn(x, hf) * (float)(1 << LO_SHIFT)));
+    const float hf = __half2float(h);
+    hi = __half_as_ushort(__float2half_rn(hf * (float)(1 << SHIFT)));
+    lo = __half_as_ushort(__float2half_rn(__fsub_rn(x, hf) * (float)(1 << SHIFT)));
 }
-__device__ __forceinline__ void split_bf16(float x, uint16_t &o0, uint16_t &o1, uint16_t &o2) {
+__device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo) {
     __nv_bfloat16 h = __float2bfloat16_rn(x);
-    float hf = __bfloat162float(h);
-    o1 = __bfloat16_as_ushort(h);
-    o0 = o1;
-    o2 = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(x, hf)));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(x, __bfloat162float(h))));
 }
-template <int PREC>
-__device__ __forceinline__ void split3(float x, uint16_t &o0, uint16_t &o1, uint16_t &o2) {
-    if (PREC == SP2_FP16_SPLIT) split_fp16(x, o0, o1, o2);
-    else split_bf16(x, o0, o1, o2);
+template <int PREC, int SHIFT>
+__device__ __forceinline__ void split2(float x, uint16_t &hi, uint16_t &lo) {
+    if (PREC == SP2_FP16_SPLIT) split_fp16<SHIFT>(x, hi, lo);
+    else split_bf16(x, hi, lo);
 }
+// Factor that turns an accumulated product back into X X (resp = 0) or X Y (resp = 1).
 template <int PREC>
-__host__ __device__ __forceinline__ float split_unscale() {
-    return PREC == SP2_FP16_SPLIT ? 1.0f / (float)(1 << LO_SHIFT) : 1.0f;
+__host__ __device__ __forceinline__ float product_unscale(bool resp) {
+    if (PREC != SP2_FP16_SPLIT) return 1.0f;
+    return resp ? 1.0f / (float)(1 << (X_SHIFT + Y_SHIFT)) : 1.0f / ((float)(1 << X_SHIFT) * (float)(1 << X_SHIFT));
 }
 
 // ---------------------------------------------------------------------------

@@ -2,12 +2,12 @@
 //
 // Device memory per instance (all row-major, padded size np = round_up(N, 128)):
 //   xf[2]       FP32 master copy of X_n, ping-pong by layer parity.
-//   xop slots   split operands of X_n, three 16-bit matrices per slot
-//               (FP16: hi * 2^11, hi, lo * 2^11;  BF16: hi, hi, lo), so that the
-//               square is one K-loop of length 3*np over A = [op0 | op1 | op2] and
-//               B = [op1 | op2 | op1] (Eq. activ: A + B + B^T with the lo*lo term
-//               dropped, all three products in one FP32 accumulator).
-//   yf[2], yop  the response / adjoint stream (FP32 master + ops 1, 2).
+//   xop slots   split operands of X_n, two 16-bit matrices per slot, hi and lo
+//               (FP16 lo stored times 2^11), so that the square is one K-loop of
+//               length 3*np over A = [hi | hi | lo] and B = [hi | lo | hi] (Eq. activ:
+//               A + B + B^T with the lo*lo term dropped, all three products in one
+//               FP32 accumulator).
+//   yf[2], yop  the response / adjoint stream (FP32 master + hi, lo).
 //   adjoint with checkpoint stride s: operand slots 0..K-1 hold X_0, X_s, ...,
 //               X_{(K-1)s} (with FP32 masters in ckf), slots K..K+s-2 the others
 //               by n mod s; the reverse sweep recomputes a segment's layers from
@@ -88,12 +88,12 @@ struct InstDesc {
     int pad_accel;
     double gap_homo, gap_lumo;
     float *xf[2];
-    uint16_t *xop;                    // slot s, op k at xop + (s*3 + k) * np * np
+    uint16_t *xop;                    // slot s: hi at xop + 2 s np^2, lo at xop + (2 s + 1) np^2
     float *yf[2];
-    uint16_t *yop;                    // slot s in {0,1}, op k
+    uint16_t *yop;                    // slot s in {0,1}: hi, lo as for xop
     Part *part[2];
     int part_cap, fin_blocks;
-    const CUtensorMap *xmap;          // [nslots_x * 3]
+    const CUtensorMap *xmap;          // [nslots_x * 3]: per slot the K segments' op0, op1, op2 = hi, hi, lo
     const CUtensorMap *ymap;          // [2 * 3]
     const double *H;                  // device copy of H (n x n)
     const double *H1;                 // response perturbation or adjoint weight (n x n)

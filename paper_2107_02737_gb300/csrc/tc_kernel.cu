@@ -5,9 +5,9 @@
 // X^(1)X^(0) (the paper's A + B + B^T; the X^(1)X^(1) term is dropped), all
 // three products accumulated in one FP32 accumulator in tensor memory:
 //   S[i,j] = sum over one K-loop of length 3*np of A[i,k] * B[j,k],
-//   A = [op0 | op1 | op2], B = [op1 | op2 | op1]   (rows of X; X is symmetric),
-// with op0 = hi*2^11, op1 = hi, op2 = lo*2^11 for FP16 (every product carries
-// 2^11, removed in the epilogue) and op0 = op1 = hi, op2 = lo for BF16.
+//   A = [hi | hi | lo], B = [hi | lo | hi]   (rows of X; X is symmetric).
+// FP16 stores both parts times 2^11 (so lo stays in FP16's normal range): every
+// product carries 2^22, removed in the epilogue.  BF16 needs no scaling.
 //
 // Centred operands and accumulator-bias removal: the FP32 accumulator of the
 // tensor cores truncates once per MMA instruction, a relative bias of order
@@ -272,7 +272,8 @@ __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams
     return w;
 }
 
-// Tensor maps of the K segment visited at position `pos`: returns the A and B maps.
+// Tensor maps of the K segment visited at position `pos`: returns the A and B maps
+// (per slot, maps op0, op1, op2 = hi, hi, lo).
 // The tensor cores' FP32 accumulator truncates once per MMA instruction, by up to
 // one unit in the last place of its current value.  The small cross-term segments
 // (hi x lo, lo x hi, 2^-11 of the result) are therefore accumulated first, while
@@ -283,16 +284,16 @@ __device__ __forceinline__ void segment_maps(const InstDesc &d, const TileWork &
                          : (int)((0x021u >> (4 * pos)) & 0xFu);     // segments 1, 2, then 0
     const CUtensorMap *X3 = d.xmap + w.xslot * 3;
     if (!w.resp) {
-        am = X3 + s;                           // op0, op1, op2
-        bm = X3 + (s == 1 ? 2 : 1);            // op1, op2, op1
+        am = X3 + s;                           // hi, hi, lo
+        bm = X3 + (s == 1 ? 2 : 1);            // hi, lo, hi
     } else {
         const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
         if (s < 3) {
-            am = X3 + s;                       // X op0, op1, op2
-            bm = Y3 + (s == 1 ? 2 : 1);        // Y op1, op2, op1
+            am = X3 + s;                       // X hi, hi, lo
+            bm = Y3 + (s == 1 ? 2 : 1);        // Y hi, lo, hi
         } else {
-            am = Y3 + (s == 4 ? 2 : 1);        // Y op1, op2, op1
-            bm = X3 + (s - 3);                 // X op0, op1, op2
+            am = Y3 + (s == 4 ? 2 : 1);        // Y hi, lo, hi
+            bm = X3 + (s - 3);                 // X hi, hi, lo
         }
     }
 }
@@ -360,7 +361,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     int pend[MAX_STAGES];               // producer: parity + 1 of a load not yet released
     for (int s = 0; s < MAX_STAGES; ++s) pend[s] = 0;
     const uint32_t idesc = idesc_f16(PREC == SP2_BF16_SPLIT ? 1u : 0u, C::TILE_M);
-    const float unscale = split_unscale<PREC>();
 
     unsigned int target = 0;
     bool first = true;
@@ -486,28 +486,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 tc_fence_after();
                 const float *__restrict__ old;
                 float *__restrict__ outf;
-                uint16_t *__restrict__ o0;
-                uint16_t *__restrict__ o1;
-                uint16_t *__restrict__ o2;
-                bool write0;
+                uint16_t *__restrict__ o1;   // hi
+                uint16_t *__restrict__ o2;   // lo
                 if (!w.resp) {
                     old = xmaster(d, w.n, w.rec != 0);
                     outf = xmaster(d, w.n + 1, w.rec != 0);
-                    uint16_t *base = d.xop + (size_t)xslot_of(d, w.n + 1) * 3 * mat;
-                    o0 = base;
-                    o1 = base + mat;
-                    o2 = base + 2 * mat;
-                    write0 = (PREC == SP2_FP16_SPLIT);
+                    o1 = d.xop + (size_t)xslot_of(d, w.n + 1) * 2 * mat;
+                    o2 = o1 + mat;
                 } else {
                     const int yout = w.ybuf ^ 1;
                     old = d.yf[w.ybuf];
                     outf = d.yf[yout];
-                    uint16_t *base = d.yop + (size_t)yout * 3 * mat;
-                    o0 = base;
-                    o1 = base + mat;
-                    o2 = base + 2 * mat;
-                    write0 = false;
+                    o1 = d.yop + (size_t)yout * 2 * mat;
+                    o2 = o1 + mat;
                 }
+                const float unscale = product_unscale<PREC>(w.resp != 0);
                 const int rw0 = w.bi * C::TILE_M + (int)rank * 128 + quarter * 32;  // first row of this warp
                 const int r = rw0 + lane;
                 const int nreal = d.n;
@@ -576,9 +569,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 if (r < c) {  // mirror (c, r): consecutive r across the warp
                                     const size_t m = (size_t)c * np + r;
                                     __stcs(outf + m, x);   // streaming stores: keep L2 for the operands
-                                    uint16_t a0, a1, a2;
-                                    split3<PREC>(y, a0, a1, a2);
-                                    if (write0) __stcs(o0 + m, a0);
+                                    uint16_t a1, a2;
+                                    if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
+                                    else split2<PREC, Y_SHIFT>(y, a1, a2);
                                     __stcs(o1 + m, a1);
                                     __stcs(o2 + m, a2);
                                 }
@@ -595,9 +588,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 const float y = (rr == cc && rr < nreal && !w.resp) ? x - 0.5f : x;
                                 const size_t m = (size_t)rr * np + cc;
                                 __stcs(outf + m, x);
-                                uint16_t a0, a1, a2;
-                                split3<PREC>(y, a0, a1, a2);
-                                if (write0) __stcs(o0 + m, a0);
+                                uint16_t a1, a2;
+                                if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
+                                else split2<PREC, Y_SHIFT>(y, a1, a2);
                                 __stcs(o1 + m, a1);
                                 __stcs(o2 + m, a2);
                             }

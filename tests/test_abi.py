@@ -46,8 +46,8 @@ def test_workspace_sizes_grow_with_n(lib):
     a = sp2.workspace_bytes(256)
     b = sp2.workspace_bytes(4096)
     assert 0 < a < b
-    # FP16 split at N = 4096: two FP32 masters + two slots of three 16-bit operands.
-    assert b >= 2 * 4096 * 4096 * 4 + 2 * 3 * 4096 * 4096 * 2
+    # FP16 split at N = 4096: two FP32 masters + two slots of two 16-bit operands (hi, lo).
+    assert b >= 2 * 4096 * 4096 * 4 + 2 * 2 * 4096 * 4096 * 2
     assert sp2.workspace_bytes(512, "adjoint", layers=10) > sp2.workspace_bytes(512, "response")
 
 
@@ -140,15 +140,17 @@ def test_batch_plan_rejects_bad_arguments_on_host(lib):
 
 
 def test_adjoint_checkpoint_workspace(lib):
-    """Keeping every s-th layer (10 bytes per element each) plus a ring of s - 1 (6 bytes)
-    and two FP32 matrices instead of every layer (6 bytes per element each)."""
+    """Keeping every s-th layer (8 bytes per element each: hi, lo and the FP32 master) plus a
+    ring of s - 1 (4 bytes) and two FP32 matrices instead of every layer (4 bytes each)."""
     n, L = 1024, 35
     mat = 1024 * 1024
     full = sp2.workspace_bytes(n, "adjoint", layers=L)
-    for s in (2, 4, 6, 9):
+    for s in (3, 4, 6, 9):
         k = L // s + 1
         got = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=s)
-        assert full - got == pytest.approx(mat * (6 * (L + 1) - 6 * (k + s - 1) - 4 * k - 8), abs=1 << 20)
+        assert full - got == pytest.approx(mat * (4 * (L + 1) - 4 * (k + s - 1) - 4 * k - 8), abs=1 << 20)
+    # stride 2 keeps 18 layers at 8 bytes: no saving over 36 at 4, so every layer is kept
+    assert sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=2) == full
     auto = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=-1)
     assert auto == min(sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=s) for s in range(2, L + 1))
     # a stride that saves nothing keeps every layer

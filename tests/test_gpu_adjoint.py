@@ -95,7 +95,7 @@ def stored_adjoints(case):
 
 
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
-@pytest.mark.parametrize("stride", [2, 3, 4, 7, -1])
+@pytest.mark.parametrize("stride", [3, 4, 5, 7, -1])
 @pytest.mark.parametrize("replay", [False, True])
 def test_checkpointed_adjoint_is_bit_identical(case, stored_adjoints, precision, stride, replay):
     ham, G, _ = case
@@ -113,7 +113,7 @@ def test_checkpointing_saves_workspace():
     auto = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=-1)
     s6 = sp2.workspace_bytes(n, "adjoint", layers=L, checkpoint_stride=6)
     assert auto <= s6 < full
-    assert auto < 0.6 * full
+    assert auto < 0.7 * full  # operands shrink 2x; FP32 masters and the second stream do not
 
 
 def test_checkpointed_adjoint_accelerated(case):

@@ -63,3 +63,35 @@ def test_unsupported_combinations():
     with pytest.raises(sp2.SP2Error) as e:
         sp2.density(H, 16.5)
     assert e.value.status == sp2.ERR_ARG
+
+
+def _raw_density(H_ptr, n, n_occ, D, o, ws=None):
+    import ctypes
+    wsp, wsb = (ctypes.c_void_p(ws.data_ptr()), ws.numel()) if ws is not None else (None, 0)
+    st = sp2._new_stats()
+    return sp2.load().sp2_density(ctypes.c_void_p(H_ptr), n, float(n_occ), 1e-6, ctypes.c_void_p(D.data_ptr()),
+                                  ctypes.byref(st), ctypes.byref(o), wsp, wsb,
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp32"])
+def test_allocation_failure_returns_nomem(precision):
+    """Host-side injection (test_hook = 2): every device allocation of the call fails."""
+    n = 256
+    ham = inputs.gapped_random(n, 128, np.random.default_rng(5))
+    H = dev(ham.H)
+    D = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    o = sp2.make_opts(precision)
+    o.test_hook = 2
+    # no workspace given: the workspace allocation fails
+    assert _raw_density(H.data_ptr(), n, 128, D, o) == sp2.ERR_NOMEM
+    # an exact workspace but a host-resident H: its staging allocation fails
+    ws = torch.empty(sp2.workspace_bytes(n, precision=precision), dtype=torch.uint8, device="cuda")
+    Hh = np.ascontiguousarray(ham.H)
+    assert _raw_density(Hh.ctypes.data, n, 128, D, o, ws) == sp2.ERR_NOMEM
+    # device-resident inputs in a caller workspace need no allocation at all
+    assert _raw_density(H.data_ptr(), n, 128, D, o, ws) == sp2.OK
+    assert fro_err(host(D), odens.density_matrix(ham.H, 128)) <= TOL_D[precision]
+    # and nothing is left behind: a normal call still works
+    D2, _ = sp2.density(H, 128, precision=precision)
+    assert torch.equal(D2, D)
