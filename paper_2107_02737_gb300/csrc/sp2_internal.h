@@ -35,7 +35,7 @@ constexpr int TC_BM = 128;          // tcgen05 tile rows (UMMA M)
 constexpr int TC_BN = 256;          // tcgen05 tile columns (UMMA N)
 constexpr int TC_BK = 64;           // K block: 64 x 16-bit = one 128-byte swizzle row
 constexpr int TC_STAGES = 4;        // TMA -> MMA pipeline depth
-constexpr int TC_THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int TC_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue (two per SM sub-partition)
 constexpr int SIMT_T = 128;         // FP32 SIMT tile (square)
 constexpr int SIMT_THREADS = 256;
 constexpr int MAX_BATCH = 128;

@@ -25,10 +25,12 @@
 //   warp 1      tcgen05.mma issuer (one thread): M=128, N=256, K=16 per
 //               instruction, FP32 accumulator in TMEM, double-buffered (2 x 256
 //               columns) so the epilogue of tile t overlaps the MMAs of t+1.
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, X_{n+1} = S or
-//               2 X_n - S, FP32 master + split operands written for the tile and
-//               its mirror (only tiles with rows <= columns are computed),
-//               compensated FP64 partials of Tr X and ||X||_F^2.
+//   warps 2..9  epilogue, two warps per SM sub-partition (the epilogue is bound by
+//               instruction latency, so a second warp hides it): warp w reads TMEM
+//               lanes 32 (w mod 4) .. +31 and the tile's column half (w - 2) / 4, in
+//               16-column chunks; X_{n+1} = S or 2 X_n - S, FP32 master + split
+//               operands written for the tile and its mirror (only tiles with rows <=
+//               columns are computed), compensated FP64 partials of Tr X and ||X||_F^2.
 // Between layers: grid barrier, then every CTA takes the same layer decision.
 // The response / adjoint stream reuses the same machinery with six K segments:
 // (C + C^T)[i,j] = sum_k X[i,k] Y[j,k] + Y[i,k] X[j,k] for symmetric X and Y.
@@ -52,9 +54,10 @@ struct Cfg {
     static constexpr int TILE_M = 128 * CG;                              // output rows per tile
 };
 constexpr int MAX_STAGES = 6;
-constexpr uint32_t EPI_T_FLOATS = 32 * 33;                // transpose buffer per epilogue warp
+constexpr int EPI_WARPS = 8;                              // warps 2..9
+constexpr int EPI_CHUNK = 16;                             // accumulator columns per epilogue step
+constexpr uint32_t EPI_T_FLOATS = 32 * (EPI_CHUNK + 1);   // transpose buffer per epilogue warp
 constexpr uint32_t TMEM_COLS = 512;                       // two 128 x 256 FP32 accumulators
-constexpr int EPI_WARPS = 4;
 
 struct TcSmemTail {
     uint64_t full[MAX_STAGES];
@@ -200,20 +203,17 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -472,8 +472,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             }
         } else {
             // --------------------------- epilogue ---------------------------
-            const int ew = warp - 2;
+            const int ew = warp - 2;                  // 0 .. EPI_WARPS - 1
             const int quarter = warp & 3;             // TMEM lanes this warp may access
+            const int half = ew >> 2;                 // column half of the tile this warp owns
             float *T = epi_T + ew * EPI_T_FLOATS;
             for (int g = cluster_id; g < rc.total; g += nclusters) {
                 const TileWork w = describe(rc, p, g);
@@ -517,23 +518,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 const float kb = al * (2.0f - al);
                 const float kc = w.flip ? al * (1.0f - 0.25f * al) : (1.0f - 0.5f * al) * (1.0f - 0.5f * al);
                 const float kx1 = fmaf(2.0f * cf, ka, kb);
-                FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f}, fp = {0.f, 0.f};
+                // ||Y||_F^2 of the next operands equals ||X||_F^2 off the diagonal (y = x
+                // there); the diagonal difference y^2 - x^2 is added in FP64 (exact squares).
+                FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fp = {0.f, 0.f};
+                double dw = 0.0;
                 if (ok && rw0 < np) {
 #pragma unroll 1
-                    for (int j = 0; j < TC_BN / 32; ++j) {
-                        const int cb = w.bj * TC_BN + j * 32;
+                    for (int j = 0; j < 128 / EPI_CHUNK; ++j) {
+                        const int c0 = half * 128 + j * EPI_CHUNK;   // column offset in the tile
+                        const int cb = w.bj * TC_BN + c0;
                         if (cb >= np) break;
-                        if (cb + 31 < rw0) continue;  // chunk entirely below the diagonal
-                        // All 32 loads of the previous layer's (r, c) values are issued
-                        // before any store of this chunk: (c, r) by symmetry, coalesced
-                        // across the warp, evict-first.
-                        float xov[32];
+                        if (cb + EPI_CHUNK - 1 < rw0) continue;  // chunk entirely below the diagonal
+                        // All loads of the previous layer's (r, c) values are issued before
+                        // any store of this chunk: (c, r) by symmetry, coalesced across the
+                        // warp, evict-first.
+                        float xov[EPI_CHUNK];
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) xov[jj] = __ldcs(old + (size_t)(cb + jj) * np + r);
-                        float v[32];
-                        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + j * 32, v);
+                        for (int jj = 0; jj < EPI_CHUNK; ++jj) xov[jj] = __ldcs(old + (size_t)(cb + jj) * np + r);
+                        float v[EPI_CHUNK];
+                        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + c0, v);
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
+                        for (int jj = 0; jj < EPI_CHUNK; ++jj) {
                             const int c = cb + jj;
                             const float P = v[jj] * unscale;            // raw product
                             const float xo = xov[jj];
@@ -560,11 +565,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             if (r <= c) {
                                 const float y = (dg && !w.resp) ? x - 0.5f : x;  // next operands
                                 if (!w.resp) {
-                                    const float wgt = (r == c) ? 1.0f : 2.0f;
+                                    ff_add_sq(fq, x, (r == c) ? 1.0f : 2.0f);
                                     if (r == c) ff_add(ft, x);
-                                    ff_add_sq(fq, x, wgt);
-                                    ff_add_sq(fw, y, wgt);
-                                    if (dg) ff_add(fp, P);
+                                    if (dg) {
+                                        ff_add(fp, P);
+                                        dw += (double)y * (double)y - (double)x * (double)x;
+                                    }
                                 }
                                 if (r < c) {  // mirror (c, r): consecutive r across the warp
                                     const size_t m = (size_t)c * np + r;
@@ -576,15 +582,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                     __stcs(o2 + m, a2);
                                 }
                             }
-                            T[lane * 33 + jj] = x;
+                            T[lane * (EPI_CHUNK + 1) + jj] = x;
                         }
                         __syncwarp();
-                        // direct (r, c) stores through the transpose buffer
+                        // direct (r, c) stores through the transpose buffer, two rows per
+                        // step: lanes 0..15 row ii, lanes 16..31 row ii + 1
+                        const int hl = lane >> 4, cl = lane & 15;
 #pragma unroll 4
-                        for (int ii = 0; ii < 32; ++ii) {
-                            const int rr = rw0 + ii, cc = cb + lane;
+                        for (int it = 0; it < 16; ++it) {
+                            const int ii = 2 * it + hl;
+                            const int rr = rw0 + ii, cc = cb + cl;
                             if (rr <= cc) {
-                                const float x = T[ii * 33 + lane];
+                                const float x = T[ii * (EPI_CHUNK + 1) + cl];
                                 const float y = (rr == cc && rr < nreal && !w.resp) ? x - 0.5f : x;
                                 const size_t m = (size_t)rr * np + cc;
                                 __stcs(outf + m, x);
@@ -611,13 +620,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     acc_phase ^= 1u;
                 }
                 if (!w.resp) {
-                    double red4[4] = {ff_value(ft), ff_value(fq), ff_value(fw), ff_value(fp)};
+                    const double q = ff_value(fq);
+                    double red4[4] = {ff_value(ft), q, q + dw, ff_value(fp)};
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         for (int o = 16; o > 0; o >>= 1) red4[k] += __shfl_down_sync(0xffffffffu, red4[k], o);
                     if (lane == 0)
                         for (int k = 0; k < 4; ++k) tl.red[ew][k] = red4[k];
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
                     if (ew == 0 && lane == 0) {
                         Part s4;
                         s4.t = s4.q = s4.w = s4.p = 0.0;
@@ -629,7 +639,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                         }
                         d.part[(w.n + 1) & 1][w.tile * CG + (int)rank] = s4;
                     }
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
                 }
             }
             // Order this round's generic-proxy stores before the async-proxy
