@@ -330,9 +330,14 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode
 
 // D = X_L (un-padded copy, diagonal offset added), FP64 partials of Tr[D H] and
 // Tr D per block; the response / adjoint output is the Y stream with its scale
-// removed.  X is stored exactly symmetric and H is symmetric, so Tr[D H] is
-// summed over the upper triangle with off-diagonal weight 2 (half the FP64 work).
+// removed.  The layer kernels keep only the lower triangle and the diagonal of
+// the FP32 masters current (the next layer reads nothing else), so the output
+// is assembled from 32 x 32 lower-triangle tiles (ti >= tj) staged in shared
+// memory: each tile is written to (ti, tj) and, transposed, to (tj, ti), both
+// with coalesced rows.  H is symmetric, so Tr[D H] is summed over the lower
+// triangle with off-diagonal weight 2.
 __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mode) {
+    __shared__ float sx[32][33], sy[32][33];
     const InstDesc &d = inst[blockIdx.y];
     if (blockIdx.x >= d.fin_blocks) return;
     const int n = d.n, np = d.np;
@@ -352,28 +357,58 @@ __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mo
     FF fe = {0.f, 0.f};
     double tr = 0.0;
     int bad_unused = 0;
-    for (int i = blockIdx.x; i < n; i += d.fin_blocks) {
-        const float *__restrict__ xrow = X + (size_t)i * np;
-        const size_t base = (size_t)i * n;
-#pragma unroll 4
-        for (int j = threadIdx.x; j < n; j += AUX_THREADS) {
-            float x = xrow[j];
-            if (i == j) {
-                x += xoff;  // true X_L = stored X_L + c_L I
-                tr += x;
+    const int tc = threadIdx.x & 31, tr0 = threadIdx.x >> 5;   // tile column, first tile row
+    const int nt = (n + 31) / 32;
+    const long long ntiles = (long long)nt * (nt + 1) / 2;
+    for (long long k = blockIdx.x; k < ntiles; k += d.fin_blocks) {
+        // k -> (ti, tj) with tj <= ti, row-major over the lower triangle of tiles
+        int ti = (int)((sqrt(8.0 * (double)k + 1.0) - 1.0) * 0.5);
+        while ((long long)(ti + 1) * (ti + 2) / 2 <= k) ++ti;
+        while ((long long)ti * (ti + 1) / 2 > k) --ti;
+        const int tj = (int)(k - (long long)ti * (ti + 1) / 2);
+        const int i0 = ti * 32, j0 = tj * 32;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = tr0 + 8 * q, i = i0 + r, j = j0 + tc;
+            float x = 0.0f, yv = 0.0f;
+            if (i < n && j < n && (ti > tj || r >= tc)) {
+                x = X[(size_t)i * np + j];
+                if (i == j) {
+                    x += xoff;  // true X_L = stored X_L + c_L I
+                    tr += x;
+                }
+                if (H) {
+                    float h1, h2;
+                    split_f64(H[(size_t)i * n + j], h1, h2, bad_unused);
+                    const float wgt = (j == i) ? 1.0f : 2.0f;
+                    const float p = __fmul_rn(x, h1);
+                    const float perr = __fmaf_rn(x, h1, -p);
+                    ff_add(fe, __fmul_rn(wgt, p));
+                    fe.c = __fadd_rn(fe.c, __fmul_rn(wgt, __fmaf_rn(x, h2 * 0x1p-24f, perr)));
+                }
+                if (second) yv = Y[(size_t)i * np + j] * ys;
             }
-            if (out) out[base + j] = x;
-            if (H && j >= i) {
-                float h1, h2;
-                split_f64(H[base + j], h1, h2, bad_unused);
-                const float wgt = (j == i) ? 1.0f : 2.0f;
-                const float p = __fmul_rn(x, h1);
-                const float perr = __fmaf_rn(x, h1, -p);
-                ff_add(fe, __fmul_rn(wgt, p));
-                fe.c = __fadd_rn(fe.c, __fmul_rn(wgt, __fmaf_rn(x, h2 * 0x1p-24f, perr)));
-            }
-            if (second) out1[base + j] = Y[(size_t)i * np + j] * ys;
+            sx[r][tc] = x;
+            sy[r][tc] = yv;
         }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = tr0 + 8 * q;
+            const bool low = (ti > tj || r >= tc);   // the diagonal tile's upper half comes transposed
+            int i = i0 + r, j = j0 + tc;
+            if (i < n && j < n) {
+                if (out) out[(size_t)i * n + j] = low ? sx[r][tc] : sx[tc][r];
+                if (second) out1[(size_t)i * n + j] = low ? sy[r][tc] : sy[tc][r];
+            }
+            i = j0 + r;
+            j = i0 + tc;
+            if (ti > tj && i < n && j < n) {        // the mirror tile (tj, ti)
+                if (out) out[(size_t)i * n + j] = sx[tc][r];
+                if (second) out1[(size_t)i * n + j] = sy[tc][r];
+            }
+        }
+        __syncthreads();
     }
     double2 s = block_sum2(ff_value(fe), tr);
     if (threadIdx.x == 0) d.fin_part[blockIdx.x] = s;

@@ -1,7 +1,9 @@
 // sp2_internal.h -- data layout shared by the host launcher and the device kernels.
 //
 // Device memory per instance (all row-major, padded size np = round_up(N, 128)):
-//   xf[2]       FP32 master copy of X_n, ping-pong by layer parity.
+//   xf[2]       FP32 master copy of X_n, ping-pong by layer parity.  The tensor-core
+//               layers keep its lower triangle and diagonal current (the next layer
+//               reads (c, r) for its tiles' r <= c); the output kernel mirrors it.
 //   xop slots   split operands of X_n, two 16-bit matrices per slot, hi and lo
 //               (FP16 lo stored times 2^11), so that the square is one K-loop of
 //               length 3*np over A = [hi | hi | lo] and B = [hi | lo | hi] (Eq. activ:

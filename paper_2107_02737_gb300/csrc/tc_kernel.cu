@@ -586,7 +586,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                         }
                         __syncwarp();
                         // direct (r, c) stores through the transpose buffer, two rows per
-                        // step: lanes 0..15 row ii, lanes 16..31 row ii + 1
+                        // step: lanes 0..15 row ii, lanes 16..31 row ii + 1.  The FP32 master
+                        // keeps only its lower triangle and diagonal (all the next layer
+                        // reads); the split operands need both triangles (TMA loads rows).
                         const int hl = lane >> 4, cl = lane & 15;
 #pragma unroll 4
                         for (int it = 0; it < 16; ++it) {
@@ -596,7 +598,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 const float x = T[ii * (EPI_CHUNK + 1) + cl];
                                 const float y = (rr == cc && rr < nreal && !w.resp) ? x - 0.5f : x;
                                 const size_t m = (size_t)rr * np + cc;
-                                __stcs(outf + m, x);
+                                if (rr == cc) __stcs(outf + m, x);
                                 uint16_t a1, a2;
                                 if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
                                 else split2<PREC, Y_SHIFT>(y, a1, a2);
