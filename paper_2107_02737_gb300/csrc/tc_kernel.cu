@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             const int ew = warp - 2;                  // 0 .. EPI_WARPS - 1
             const int quarter = warp & 3;             // TMEM lanes this warp may access
             const int half = ew >> 2;                 // column half of the tile this warp owns
-            float *T = epi_T + ew * EPI_T_FLOATS;
+            uint32_t *T = (uint32_t *)(epi_T + ew * EPI_T_FLOATS);   // packed split operands
             for (int g = cluster_id; g < rc.total; g += nclusters) {
                 const TileWork w = describe(rc, p, g);
                 const InstDesc &d = p.inst[w.inst];
@@ -537,73 +537,110 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                         for (int jj = 0; jj < EPI_CHUNK; ++jj) xov[jj] = __ldcs(old + (size_t)(cb + jj) * np + r);
                         float v[EPI_CHUNK];
                         tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + c0, v);
+                        // Each element's next split operands are computed once, stored to the
+                        // mirror (c, r) and staged packed (hi | lo << 16) for the direct (r, c)
+                        // stores below.  The FP32 master gets the mirror and the diagonal only.
+                        const bool upper = (cb > rw0 + 31);     // every element has r < c
+                        if (upper && !w.resp && !accel) {
+                            // The common case: a plain square-chain layer, strictly upper chunk.
+                            const float twoc = 2.0f * cf;
 #pragma unroll
-                        for (int jj = 0; jj < EPI_CHUNK; ++jj) {
-                            const int c = cb + jj;
-                            const float P = v[jj] * unscale;            // raw product
-                            const float xo = xov[jj];
-                            const bool dg = (r == c) && (r < nreal);
-                            float x;
-                            if (!w.resp) {
-                                // P = Y^2 for the stored operands Y = X - I/2; the true input is
-                                // X + cI, so X^2 = P + 2cY + cI + X - I/4 (c^2 is below FP32 here).
-                                const float yo = dg ? xo - 0.5f : xo;
-                                if (accel) {
-                                    x = fmaf(ka, fmaf(2.0f * cf, yo, P), fmaf(kb, dg ? yo + cf : yo, dg ? kc : 0.0f));
-                                } else {
-                                    const float b = dg ? P - 0.25f : P;
-                                    if (!w.flip) x = (b + fmaf(2.0f * cf, yo, dg ? cf : 0.0f)) + xo;  // X^2
-                                    else x = xo - (b + fmaf(2.0f * cf, yo, dg ? -cf : 0.0f));        // 2X - X^2
-                                }
-                            } else if (accel) {
-                                x = fmaf(kx1, xo, ka * P);
-                            } else {
-                                // P = Y X1 + X1 Y; with X = Y + (1/2 + c) I the chain needs
-                                // X X1 + X1 X = P + (1 + 2c) X1.
-                                x = w.flip ? fmaf(1.0f - 2.0f * cf, xo, -P) : fmaf(1.0f + 2.0f * cf, xo, P);
+                            for (int jj = 0; jj < EPI_CHUNK; ++jj) {
+                                const int c = cb + jj;
+                                const float xo = xov[jj];
+                                const float t = fmaf(twoc, xo, v[jj] * unscale);
+                                const float x = w.flip ? xo - t : t + xo;   // 2X - X^2 or X^2
+                                ff_add_sq(fq, x, 2.0f);
+                                const size_t m = (size_t)c * np + r;
+                                __stcs(outf + m, x);
+                                uint16_t a1, a2;
+                                split2<PREC, X_SHIFT>(x, a1, a2);
+                                __stcs(o1 + m, a1);
+                                __stcs(o2 + m, a2);
+                                T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
                             }
-                            if (r <= c) {
-                                const float y = (dg && !w.resp) ? x - 0.5f : x;  // next operands
+                        } else if (upper && w.resp && !accel) {
+                            // Response / adjoint stream, plain layer, strictly upper chunk:
+                            // X X1 + X1 X = P + (1 + 2c) X1, negated for 2X - X^2 (as below).
+                            const float kx = w.flip ? 1.0f - 2.0f * cf : 1.0f + 2.0f * cf;
+                            const float sg = w.flip ? -unscale : unscale;
+#pragma unroll
+                            for (int jj = 0; jj < EPI_CHUNK; ++jj) {
+                                const int c = cb + jj;
+                                const float x = fmaf(kx, xov[jj], v[jj] * sg);
+                                const size_t m = (size_t)c * np + r;
+                                __stcs(outf + m, x);
+                                uint16_t a1, a2;
+                                split2<PREC, Y_SHIFT>(x, a1, a2);
+                                __stcs(o1 + m, a1);
+                                __stcs(o2 + m, a2);
+                                T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
+                            }
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < EPI_CHUNK; ++jj) {
+                                const int c = cb + jj;
+                                const float P = v[jj] * unscale;            // raw product
+                                const float xo = xov[jj];
+                                const bool dg = (r == c) && (r < nreal);
+                                float x;
                                 if (!w.resp) {
-                                    ff_add_sq(fq, x, (r == c) ? 1.0f : 2.0f);
-                                    if (r == c) ff_add(ft, x);
-                                    if (dg) {
-                                        ff_add(fp, P);
-                                        dw += (double)y * (double)y - (double)x * (double)x;
+                                    // P = Y^2 for the stored operands Y = X - I/2; the true input is
+                                    // X + cI, so X^2 = P + 2cY + cI + X - I/4 (c^2 is below FP32 here).
+                                    const float yo = dg ? xo - 0.5f : xo;
+                                    if (accel) {
+                                        x = fmaf(ka, fmaf(2.0f * cf, yo, P), fmaf(kb, dg ? yo + cf : yo, dg ? kc : 0.0f));
+                                    } else {
+                                        const float b = dg ? P - 0.25f : P;
+                                        if (!w.flip) x = (b + fmaf(2.0f * cf, yo, dg ? cf : 0.0f)) + xo;  // X^2
+                                        else x = xo - (b + fmaf(2.0f * cf, yo, dg ? -cf : 0.0f));        // 2X - X^2
                                     }
+                                } else if (accel) {
+                                    x = fmaf(kx1, xo, ka * P);
+                                } else {
+                                    // P = Y X1 + X1 Y; with X = Y + (1/2 + c) I the chain needs
+                                    // X X1 + X1 X = P + (1 + 2c) X1.
+                                    x = w.flip ? fmaf(1.0f - 2.0f * cf, xo, -P) : fmaf(1.0f + 2.0f * cf, xo, P);
                                 }
-                                if (r < c) {  // mirror (c, r): consecutive r across the warp
+                                const float y = (dg && !w.resp) ? x - 0.5f : x;  // next operands
+                                uint16_t a1, a2;
+                                if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
+                                else split2<PREC, Y_SHIFT>(y, a1, a2);
+                                if (r <= c) {
+                                    if (!w.resp) {
+                                        ff_add_sq(fq, x, (r == c) ? 1.0f : 2.0f);
+                                        if (r == c) ff_add(ft, x);
+                                        if (dg) {
+                                            ff_add(fp, P);
+                                            dw += (double)y * (double)y - (double)x * (double)x;
+                                        }
+                                    }
+                                    // mirror (c, r), consecutive r across the warp; the diagonal
+                                    // element's FP32 master value here too
                                     const size_t m = (size_t)c * np + r;
                                     __stcs(outf + m, x);   // streaming stores: keep L2 for the operands
-                                    uint16_t a1, a2;
-                                    if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
-                                    else split2<PREC, Y_SHIFT>(y, a1, a2);
-                                    __stcs(o1 + m, a1);
-                                    __stcs(o2 + m, a2);
+                                    if (r < c) {
+                                        __stcs(o1 + m, a1);
+                                        __stcs(o2 + m, a2);
+                                    }
                                 }
+                                T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
                             }
-                            T[lane * (EPI_CHUNK + 1) + jj] = x;
                         }
                         __syncwarp();
-                        // direct (r, c) stores through the transpose buffer, two rows per
-                        // step: lanes 0..15 row ii, lanes 16..31 row ii + 1.  The FP32 master
-                        // keeps only its lower triangle and diagonal (all the next layer
-                        // reads); the split operands need both triangles (TMA loads rows).
+                        // direct (r, c) split-operand stores through the transpose buffer, two
+                        // rows per step: lanes 0..15 row ii, lanes 16..31 row ii + 1 (the
+                        // operands need both triangles: TMA loads rows)
                         const int hl = lane >> 4, cl = lane & 15;
 #pragma unroll 4
                         for (int it = 0; it < 16; ++it) {
                             const int ii = 2 * it + hl;
                             const int rr = rw0 + ii, cc = cb + cl;
-                            if (rr <= cc) {
-                                const float x = T[ii * (EPI_CHUNK + 1) + cl];
-                                const float y = (rr == cc && rr < nreal && !w.resp) ? x - 0.5f : x;
+                            if (upper || rr <= cc) {
+                                const uint32_t pk = T[ii * (EPI_CHUNK + 1) + cl];
                                 const size_t m = (size_t)rr * np + cc;
-                                if (rr == cc) __stcs(outf + m, x);
-                                uint16_t a1, a2;
-                                if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
-                                else split2<PREC, Y_SHIFT>(y, a1, a2);
-                                __stcs(o1 + m, a1);
-                                __stcs(o2 + m, a2);
+                                __stcs(o1 + m, (uint16_t)(pk & 0xFFFFu));
+                                __stcs(o2 + m, (uint16_t)(pk >> 16));
                             }
                         }
                         __syncwarp();
