@@ -239,13 +239,14 @@ __device__ __forceinline__ void round_ctl_init(RoundCtl &rc, const RunParams &p)
 
 // All threads of a CTA: sum, for every instance still running, the per-tile
 // partials of the layer just finished into sums[4 i .. 4 i + 3] (shared memory).
-// Thread k adds entries k, k + blockDim.x, ... in increasing order, then a fixed
-// shuffle tree and a fixed sum over warps: the same code on every CTA gives the
-// same bits, so every CTA takes the same decision.
-__device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams &p, double *sums, double *wscratch) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+// One warp per instance (warp w takes instances w, w + nwarps, ...): lane l adds
+// entries l, l + 32, ... in increasing order, then a fixed shuffle tree.  The
+// order depends only on the instance's own partials, so every CTA -- and a batch
+// or a lone call alike -- gets the same bits and takes the same decision.
+__device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams &p, double *sums) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (rc.phase == 1) return;
-    for (int i = 0; i < p.B; ++i) {
+    for (int i = wid; i < p.B; i += nw) {
         if (!rc.active[i]) continue;
         const InstDesc &d = p.inst[i];
         const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
@@ -253,7 +254,7 @@ __device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams
         const Part *part = d.part[n & 1];
         double a[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 4
-        for (int k = tid; k < cnt; k += blockDim.x) {
+        for (int k = lane; k < cnt; k += 32) {
             const Part v = part[k];
             a[0] += v.t;
             a[1] += v.q;
@@ -264,20 +265,19 @@ __device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams
         for (int c = 0; c < 4; ++c)
             for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
         if (lane == 0)
-            for (int c = 0; c < 4; ++c) wscratch[wid * 4 + c] = a[c];
-        __syncthreads();
-        if (tid == 0) {
-            double r[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int w = 0; w < nw; ++w)
-                for (int c = 0; c < 4; ++c) r[c] += wscratch[w * 4 + c];
-            for (int c = 0; c < 4; ++c) sums[i * 4 + c] = r[c];
-        }
-        __syncthreads();
+            for (int c = 0; c < 4; ++c) sums[i * 4 + c] = a[c];
     }
+    __syncthreads();
 }
 
-// Thread 0 of every CTA: take the sums of the layer just finished, record
-// statistics (CTA 0), apply the stop rule and pick the next signs.
+// The decision for instance i from the sums of the layer just finished: record
+// its statistics (CTA 0), apply the stop rule and pick the next sign.  Returns
+// the number of tiles instance i computes this round, or -1 when an adjoint
+// forward chain stopped and the round was set up for the reverse sweep.
+__device__ inline int decide_instance(RoundCtl &rc, const RunParams &p, const double *sums, int i, bool writer);
+
+// Thread 0 of every CTA: the whole round's decision, instance by instance (the
+// adjoint's reverse sweep and its switch to it live here; that path has B = 1).
 __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const double *sums) {
     const bool writer = (blockIdx.x == 0);
     if (ld_volatile(p.err) != 0) {
@@ -320,140 +320,169 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const doub
     int acc = 0;
     rc.prefix[0] = 0;
     for (int i = 0; i < p.B; ++i) {
-        const InstDesc &d = p.inst[i];
-        InstCtl *ctl = d.ctl;
-        int width = 0;
-        if (rc.active[i]) {
-            if (rc.ran[i]) rc.layer[i] += 1;
-            const int n = rc.layer[i];
-            const double ts = sums[i * 4 + 0], qs = sums[i * 4 + 1], ws = sums[i * 4 + 2], ps = sums[i * 4 + 3];
-            const int made = (n == 0) ? SP2_CHOICE_INPUT : rc.choice[i];
-            // Accumulator bias of the square that made X_n: in exact arithmetic
-            // Tr(Y^2) = ||Y||_F^2 for the symmetric operand Y, so the deficit of the
-            // computed trace, spread over the N diagonal entries, is the identity
-            // component of the product error.  It is removed as the offset c_n of
-            // X_n (sign of the layer: X^2 keeps it, 2X - X^2 negates it).  Both
-            // sums are zero on the FP32 path, where c_n stays 0.
-            // An accelerated layer multiplies the product by +-a^2 (X^2: +, 2X - X^2: -).
-            double c = 0.0;
-            const float a_made = (n == 0) ? 1.0f : rc.alpha[i];
-            if (n > 0) {
-                const double gam = (rc.wprev[i] - ps) / (double)d.n;
-                const double a2 = (double)a_made * (double)a_made;
-                c = (made == SP2_CHOICE_SQUARE) ? a2 * gam : -a2 * gam;
-            }
-            const double t = ts + (double)d.n * c;
-            const double q = qs + 2.0 * c * ts + (double)d.n * c * c;
-            rc.wprev[i] = ws;
-            rc.coff[i] = c;
-            rc.chist_c[n] = c;
-            if (writer) {
-                LayerStatDev st;
-                st.trace = t;
-                st.trace_sq = q;
-                st.idem = t - q;
-                st.choice = made;
-                st.reserved = 0;
-                st.alpha = (double)a_made;
-                ctl->stat[n] = st;
-            }
-            rc.chist[n] = (signed char)made;
-            rc.chist_a[n] = a_made;
-            const double e = fabs(t - q);
-            const double e2 = rc.ehist[i][n & 1];
-            rc.ehist[i][n & 1] = e;
-            int reason = 0, status = 0;
-            bool stop = false;
-            if (!isfinite(t) || !isfinite(q)) {
-                stop = true;
-                status = SP2_ERR_NONFINITE;
-            } else if (ctl->degenerate) {
-                stop = true;
-                status = SP2_ERR_NOT_CONVERGED;
-                reason = SP2_STOP_MAX;
-            } else if (d.nforced >= 0) {
-                if (n >= d.nforced) {
-                    stop = true;
-                    if (e <= p.tol) reason = SP2_STOP_TOL;
-                    else if (n >= 2 && e <= STALL_MAX && e >= e2) reason = SP2_STOP_STALL;
-                    else reason = SP2_STOP_NONE;
-                }
-            } else if (e <= p.tol) {
-                stop = true;
-                reason = SP2_STOP_TOL;
-            } else if (n >= 2 && e <= STALL_MAX && e >= e2) {
-                stop = true;
-                reason = SP2_STOP_STALL;
-            } else if (n >= p.max_layers) {
-                stop = true;
-                reason = SP2_STOP_MAX;
-                status = SP2_ERR_NOT_CONVERGED;
-            }
-            if (stop) {
-                rc.active[i] = 0;
-                rc.ran[i] = 0;
-                if (writer) {
-                    ctl->layers = n;
-                    ctl->stop_reason = reason;
-                    ctl->status = status;
-                    ctl->final_x = n & 1;
-                    ctl->final_y = n & 1;
-                    ctl->x_offset = c;
-                }
-                if (p.mode == MODE_ADJOINT && status == 0) {
-                    // Switch to the reverse sweep: G_L is in Y buffer 0.  Reverse round
-                    // k (= layer[0]) maps G_{m+1} to G_m with m = L - 1 - k, reading Y
-                    // buffer k & 1 and X_m from slot m.
-                    rc.phase = 1;
-                    rc.rev_total = n;
-                    rc.rev_left = n;
-                    rc.layer[0] = 0;
-                    // The forward chain left X_{s floor((L-1)/s)} .. X_{L-1} in place.
-                    rc.rec_mode = 0;
-                    rc.rec_seg = (d.ckpt_s > 0 && n > 0) ? (n - 1) / d.ckpt_s : 0;
-                    rc.rec_top = n - 1;
-                    rc.prefix[1] = 0;
-                    rc.total = 0;
-                    if (n == 0) {
-                        if (writer) ctl->final_y = 0;
-                        return;
-                    }
-                    rc.jobs[0] = 1;
-                    rc.prefix[1] = d.ntiles;
-                    rc.total = d.ntiles;
-                    return;
-                }
-            } else {
-                const int c = (d.nforced >= 0) ? d.forced[n] : layer_rule(t, q, d.n_occ);
-                rc.choice[i] = (signed char)c;
-                // Expansion of the accelerated layer: the tracked ends of the interval
-                // are balanced around the branch's fixed point, then follow the layer.
-                float a = 1.0f;
-                if (d.nforced >= 0 && d.forced_alpha) {
-                    a = (float)d.forced_alpha[n];
-                } else if (d.accel) {
-                    a = (c == SP2_CHOICE_SQUARE) ? 2.0f / (2.0f - rc.xl[i]) : 2.0f / (1.0f + rc.xh[i]);
-                    if (c == SP2_CHOICE_SQUARE) {
-                        const float tl = fmaf(a, rc.xl[i], 1.0f - a), th = fmaf(a, rc.xh[i], 1.0f - a);
-                        rc.xl[i] = tl * tl;
-                        rc.xh[i] = th * th;
-                    } else {
-                        const float tl = a * rc.xl[i], th = a * rc.xh[i];
-                        rc.xl[i] = fmaf(-tl, tl, 2.0f * tl);
-                        rc.xh[i] = fmaf(-th, th, 2.0f * th);
-                    }
-                }
-                rc.alpha[i] = a;
-                rc.ran[i] = 1;
-                rc.jobs[i] = (p.mode == MODE_RESPONSE) ? 2 : 1;
-                width = rc.jobs[i] * d.ntiles;
-            }
-        }
-        if (!rc.active[i]) rc.jobs[i] = 0;
+        const int width = decide_instance(rc, p, sums, i, writer);
+        if (width < 0) return;
         acc += width;
         rc.prefix[i + 1] = acc;
     }
     rc.total = acc;
+}
+
+__device__ inline int decide_instance(RoundCtl &rc, const RunParams &p, const double *sums, int i, bool writer) {
+    const InstDesc &d = p.inst[i];
+    InstCtl *ctl = d.ctl;
+    int width = 0;
+    if (rc.active[i]) {
+        if (rc.ran[i]) rc.layer[i] += 1;
+        const int n = rc.layer[i];
+        const double ts = sums[i * 4 + 0], qs = sums[i * 4 + 1], ws = sums[i * 4 + 2], ps = sums[i * 4 + 3];
+        const int made = (n == 0) ? SP2_CHOICE_INPUT : rc.choice[i];
+        // Accumulator bias of the square that made X_n: in exact arithmetic
+        // Tr(Y^2) = ||Y||_F^2 for the symmetric operand Y, so the deficit of the
+        // computed trace, spread over the N diagonal entries, is the identity
+        // component of the product error.  It is removed as the offset c_n of
+        // X_n (sign of the layer: X^2 keeps it, 2X - X^2 negates it).  Both
+        // sums are zero on the FP32 path, where c_n stays 0.
+        // An accelerated layer multiplies the product by +-a^2 (X^2: +, 2X - X^2: -).
+        double c = 0.0;
+        const float a_made = (n == 0) ? 1.0f : rc.alpha[i];
+        if (n > 0) {
+            const double gam = (rc.wprev[i] - ps) / (double)d.n;
+            const double a2 = (double)a_made * (double)a_made;
+            c = (made == SP2_CHOICE_SQUARE) ? a2 * gam : -a2 * gam;
+        }
+        const double t = ts + (double)d.n * c;
+        const double q = qs + 2.0 * c * ts + (double)d.n * c * c;
+        rc.wprev[i] = ws;
+        rc.coff[i] = c;
+        if (p.B == 1) rc.chist_c[n] = c;  // layer history for the adjoint (one instance)
+        if (writer) {
+            LayerStatDev st;
+            st.trace = t;
+            st.trace_sq = q;
+            st.idem = t - q;
+            st.choice = made;
+            st.reserved = 0;
+            st.alpha = (double)a_made;
+            ctl->stat[n] = st;
+        }
+        if (p.B == 1) {
+            rc.chist[n] = (signed char)made;
+            rc.chist_a[n] = a_made;
+        }
+        const double e = fabs(t - q);
+        const double e2 = rc.ehist[i][n & 1];
+        rc.ehist[i][n & 1] = e;
+        int reason = 0, status = 0;
+        bool stop = false;
+        if (!isfinite(t) || !isfinite(q)) {
+            stop = true;
+            status = SP2_ERR_NONFINITE;
+        } else if (ctl->degenerate) {
+            stop = true;
+            status = SP2_ERR_NOT_CONVERGED;
+            reason = SP2_STOP_MAX;
+        } else if (d.nforced >= 0) {
+            if (n >= d.nforced) {
+                stop = true;
+                if (e <= p.tol) reason = SP2_STOP_TOL;
+                else if (n >= 2 && e <= STALL_MAX && e >= e2) reason = SP2_STOP_STALL;
+                else reason = SP2_STOP_NONE;
+            }
+        } else if (e <= p.tol) {
+            stop = true;
+            reason = SP2_STOP_TOL;
+        } else if (n >= 2 && e <= STALL_MAX && e >= e2) {
+            stop = true;
+            reason = SP2_STOP_STALL;
+        } else if (n >= p.max_layers) {
+            stop = true;
+            reason = SP2_STOP_MAX;
+            status = SP2_ERR_NOT_CONVERGED;
+        }
+        if (stop) {
+            rc.active[i] = 0;
+            rc.ran[i] = 0;
+            if (writer) {
+                ctl->layers = n;
+                ctl->stop_reason = reason;
+                ctl->status = status;
+                ctl->final_x = n & 1;
+                ctl->final_y = n & 1;
+                ctl->x_offset = c;
+            }
+            if (p.mode == MODE_ADJOINT && status == 0) {
+                // Switch to the reverse sweep: G_L is in Y buffer 0.  Reverse round
+                // k (= layer[0]) maps G_{m+1} to G_m with m = L - 1 - k, reading Y
+                // buffer k & 1 and X_m from slot m.
+                rc.phase = 1;
+                rc.rev_total = n;
+                rc.rev_left = n;
+                rc.layer[0] = 0;
+                // The forward chain left X_{s floor((L-1)/s)} .. X_{L-1} in place.
+                rc.rec_mode = 0;
+                rc.rec_seg = (d.ckpt_s > 0 && n > 0) ? (n - 1) / d.ckpt_s : 0;
+                rc.rec_top = n - 1;
+                rc.prefix[1] = 0;
+                rc.total = 0;
+                if (n == 0) {
+                    if (writer) ctl->final_y = 0;
+                    return -1;
+                }
+                rc.jobs[0] = 1;
+                rc.prefix[1] = d.ntiles;
+                rc.total = d.ntiles;
+                return -1;
+            }
+        } else {
+            const int c = (d.nforced >= 0) ? d.forced[n] : layer_rule(t, q, d.n_occ);
+            rc.choice[i] = (signed char)c;
+            // Expansion of the accelerated layer: the tracked ends of the interval
+            // are balanced around the branch's fixed point, then follow the layer.
+            float a = 1.0f;
+            if (d.nforced >= 0 && d.forced_alpha) {
+                a = (float)d.forced_alpha[n];
+            } else if (d.accel) {
+                a = (c == SP2_CHOICE_SQUARE) ? 2.0f / (2.0f - rc.xl[i]) : 2.0f / (1.0f + rc.xh[i]);
+                if (c == SP2_CHOICE_SQUARE) {
+                    const float tl = fmaf(a, rc.xl[i], 1.0f - a), th = fmaf(a, rc.xh[i], 1.0f - a);
+                    rc.xl[i] = tl * tl;
+                    rc.xh[i] = th * th;
+                } else {
+                    const float tl = a * rc.xl[i], th = a * rc.xh[i];
+                    rc.xl[i] = fmaf(-tl, tl, 2.0f * tl);
+                    rc.xh[i] = fmaf(-th, th, 2.0f * th);
+                }
+            }
+            rc.alpha[i] = a;
+            rc.ran[i] = 1;
+            rc.jobs[i] = (p.mode == MODE_RESPONSE) ? 2 : 1;
+            width = rc.jobs[i] * d.ntiles;
+        }
+    }
+    if (!rc.active[i]) rc.jobs[i] = 0;
+    return width;
+}
+
+// All threads of every CTA: the round's decision with one thread per instance
+// (density, response and layer-application runs; the adjoint, a single instance,
+// goes through decide_round).  `wbuf` holds MAX_BATCH ints of shared memory.
+__device__ inline void decide_round_parallel(RoundCtl &rc, const RunParams &p, const double *sums, int *wbuf) {
+    if (threadIdx.x == 0 && ld_volatile(p.err) != 0) rc.abort = 1;
+    __syncthreads();
+    if (rc.abort) return;
+    const bool writer = (blockIdx.x == 0);
+    for (int i = threadIdx.x; i < p.B; i += blockDim.x) wbuf[i] = decide_instance(rc, p, sums, i, writer);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        rc.prefix[0] = 0;
+        for (int i = 0; i < p.B; ++i) {
+            acc += wbuf[i];
+            rc.prefix[i + 1] = acc;
+        }
+        rc.total = acc;
+    }
 }
 
 // Map a round-global tile index to (instance, job, tile).

@@ -73,6 +73,8 @@ struct TcSmemTail {
 constexpr size_t STAGE_AREA = 196608;  // 4 x 48 KB or 6 x 32 KB
 static_assert(Cfg<1>::STAGES * Cfg<1>::STAGE_BYTES <= STAGE_AREA, "stage area");
 static_assert(Cfg<2>::STAGES * Cfg<2>::STAGE_BYTES <= STAGE_AREA, "stage area");
+static_assert(EPI_WARPS * EPI_T_FLOATS * 4 >= 4 * MAX_BATCH * sizeof(double) + MAX_BATCH * sizeof(int),
+              "round sums and decisions reuse the epilogue transpose buffers");
 constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGE_AREA + (size_t)EPI_WARPS * EPI_T_FLOATS * 4 +
                               sizeof(TcSmemTail);
 
@@ -377,9 +379,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         }
         first = false;
         // The epilogue transpose buffers are idle here: use them for the sums.
-        reduce_round_partials(rc, p, (double *)epi_T, (double *)epi_T + 4 * MAX_BATCH);
+        reduce_round_partials(rc, p, (double *)epi_T);
+        if (p.mode == MODE_ADJOINT) {
+            if (threadIdx.x == 0) decide_round(rc, p, (const double *)epi_T);
+        } else {
+            decide_round_parallel(rc, p, (const double *)epi_T, (int *)((double *)epi_T + 4 * MAX_BATCH));
+        }
         if (threadIdx.x == 0) {
-            decide_round(rc, p, (const double *)epi_T);
             // Make the previous round's global writes (other CTAs' epilogues,
             // generic proxy) visible to this CTA's TMA reads (async proxy).
             asm volatile("fence.proxy.async.global;" ::: "memory");
