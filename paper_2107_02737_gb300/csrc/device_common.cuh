@@ -274,7 +274,7 @@ __device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams
 // its statistics (CTA 0), apply the stop rule and pick the next sign.  Returns
 // the number of tiles instance i computes this round, or -1 when an adjoint
 // forward chain stopped and the round was set up for the reverse sweep.
-__device__ inline int decide_instance(RoundCtl &rc, const RunParams &p, const double *sums, int i, bool writer);
+static __device__ __noinline__ int decide_instance(RoundCtl &rc, const RunParams &p, const double *sums, int i, bool writer);
 
 // Thread 0 of every CTA: the whole round's decision, instance by instance (the
 // adjoint's reverse sweep and its switch to it live here; that path has B = 1).
@@ -328,7 +328,9 @@ __device__ inline void decide_round(RoundCtl &rc, const RunParams &p, const doub
     rc.total = acc;
 }
 
-__device__ inline int decide_instance(RoundCtl &rc, const RunParams &p, const double *sums, int i, bool writer) {
+// Compiled out of line: inlined into the persistent kernels it raises their
+// register allocation (the FP32 kernel then drops from two CTAs per SM to one).
+static __device__ __noinline__ int decide_instance(RoundCtl &rc, const RunParams &p, const double *sums, int i, bool writer) {
     const InstDesc &d = p.inst[i];
     InstCtl *ctl = d.ctl;
     int width = 0;
@@ -482,6 +484,47 @@ __device__ inline void decide_round_parallel(RoundCtl &rc, const RunParams &p, c
             rc.prefix[i + 1] = acc;
         }
         rc.total = acc;
+    }
+}
+
+// All threads of a CTA, for the FP32 CUDA-core kernel: the same sums with thread k
+// adding entries k, k + blockDim.x, ..., a fixed shuffle tree and a fixed sum over
+// warps, instance after instance.  That kernel runs two CTAs per SM, and there
+// one warp per instance over its 2N^2/128^2 partials costs more than the
+// block-wide pass (measured: +56 ms over a 32-layer chain at N = 8192).  The order
+// again depends only on the instance's partials and the block size.
+__device__ inline void reduce_round_partials_block(const RoundCtl &rc, const RunParams &p, double *sums,
+                                                   double *wscratch) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (rc.phase == 1) return;
+    for (int i = 0; i < p.B; ++i) {
+        if (!rc.active[i]) continue;
+        const InstDesc &d = p.inst[i];
+        const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
+        const int cnt = (n == 0) ? d.ctl->init_parts : d.parts;
+        const Part *part = d.part[n & 1];
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+        for (int k = tid; k < cnt; k += blockDim.x) {
+            const Part v = part[k];
+            a[0] += v.t;
+            a[1] += v.q;
+            a[2] += v.w;
+            a[3] += v.p;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+        if (lane == 0)
+            for (int c = 0; c < 4; ++c) wscratch[wid * 4 + c] = a[c];
+        __syncthreads();
+        if (tid == 0) {
+            double r[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int w = 0; w < nw; ++w)
+                for (int c = 0; c < 4; ++c) r[c] += wscratch[w * 4 + c];
+            for (int c = 0; c < 4; ++c) sums[i * 4 + c] = r[c];
+        }
+        __syncthreads();
     }
 }
 

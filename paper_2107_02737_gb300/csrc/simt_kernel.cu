@@ -21,8 +21,8 @@ struct SimtSmem {
     float B[2][BK][LDS];
     double red[SIMT_THREADS / 32][2];
 };
-static_assert(sizeof(float) * 2 * BK * LDS >= 4 * MAX_BATCH * sizeof(double) + MAX_BATCH * sizeof(int),
-              "round sums and decisions reuse the A staging buffers");
+static_assert(sizeof(float) * 2 * BK * LDS >= 4 * MAX_BATCH * sizeof(double) + 4 * (SIMT_THREADS / 32) * sizeof(double),
+              "round sums reuse the A staging buffers");
 
 // acc = Y^2 over the tile for the centred operand Y = X - I/2 (I on the n real
 // diagonal entries): Y has the eigenvalues of X shifted into [-1/2, 1/2], so the
@@ -132,6 +132,8 @@ __device__ __forceinline__ void simt_tile_epilogue(const float *__restrict__ Xol
     }
 }
 
+// Two CTAs per SM at 128 registers per thread (the comparator's throughput halves
+// at one; a launch bound forcing it makes the kernel spill and costs 4 %).
 __global__ void __launch_bounds__(SIMT_THREADS) k_simt_persistent(const __grid_constant__ RunParams p) {
     __shared__ RoundCtl rc;
     __shared__ __align__(16) SimtSmem sm;
@@ -153,8 +155,8 @@ __global__ void __launch_bounds__(SIMT_THREADS) k_simt_persistent(const __grid_c
         first = false;
         // The operand staging buffers are idle here: use them for the sums.
         double *sums = (double *)&sm.A[0][0][0];
-        reduce_round_partials(rc, p, sums);
-        decide_round_parallel(rc, p, sums, (int *)(sums + 4 * MAX_BATCH));
+        reduce_round_partials_block(rc, p, sums, sums + 4 * MAX_BATCH);
+        if (threadIdx.x == 0) decide_round(rc, p, sums);
         __syncthreads();
         if (rc.abort || rc.total == 0) break;
         for (int g = blockIdx.x; g < rc.total; g += gridDim.x) {
