@@ -403,11 +403,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     const int nseg = w.resp ? 6 : 3;
                     const int row_a = w.bi * C::TILE_M + (int)rank * 128;
                     const int row_b = w.bj * TC_BN + (CG == 2 ? (int)rank * 128 : 0);
-                    for (int kb = 0; kb < nseg * nkb; ++kb) {
-                        const int s = kb / nkb;
-                        const int kx = (kb - s * nkb) * TC_BK;
+                    // Square tiles: each K block in two consecutive ring slots, (hi, hi) then
+                    // (lo, lo), which feed all three products.  Response tiles: the six
+                    // segments one after another, one K block per slot.
+                    const int nslot = w.resp ? nseg * nkb : 2 * nkb;
+                    for (int kb = 0; kb < nslot; ++kb) {
+                        int kx;
                         const CUtensorMap *am, *bm;
-                        segment_maps(d, w, s, am, bm);
+                        if (w.resp) {
+                            const int s = kb / nkb;
+                            kx = (kb - s * nkb) * TC_BK;
+                            segment_maps(d, w, s, am, bm);
+                        } else {
+                            const CUtensorMap *X3 = d.xmap + w.xslot * 3;   // maps hi, hi, lo
+                            kx = (kb >> 1) * TC_BK;
+                            am = bm = (kb & 1) ? X3 + 2 : X3 + 1;
+                        }
                         if (!mbar_wait(&tl.empty[stage], phase ^ 1u, abort, p.timeout_ns, p.err)) {
                             rc.abort = 1;
                             break;
@@ -448,7 +459,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + acc * TC_BN;
                     bool ok = true;
-                    for (int kb = 0; kb < nkb; ++kb) {
+                    if (!w.resp) {
+                        // Square: per K block the (hi, hi) and (lo, lo) slots, then hi lo, lo hi
+                        // (the small cross terms first) and hi hi.
+                        for (int kb = 0; kb < d.np / TC_BK; ++kb) {
+                            uint32_t sh, sl;
+                            const uint32_t st_h = stage;
+                            if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                                rc.abort = 1;
+                                ok = false;
+                                break;
+                            }
+                            sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                            if (++stage == C::STAGES) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                            const uint32_t st_l = stage;
+                            if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                                rc.abort = 1;
+                                ok = false;
+                                break;
+                            }
+                            sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                            if (++stage == C::STAGES) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                            tc_fence_after();
+#pragma unroll
+                            for (int k = 0; k < TC_BK / 16; ++k)   // hi x lo
+                                umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32), sdesc_sw128(sl + C::A_BYTES + k * 32),
+                                             idesc, (kb | k) != 0 ? 1u : 0u);
+#pragma unroll
+                            for (int k = 0; k < TC_BK / 16; ++k)   // lo x hi
+                                umma_f16<CG>(d_tmem, sdesc_sw128(sl + k * 32), sdesc_sw128(sh + C::A_BYTES + k * 32),
+                                             idesc, 1u);
+#pragma unroll
+                            for (int k = 0; k < TC_BK / 16; ++k)   // hi x hi
+                                umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32), sdesc_sw128(sh + C::A_BYTES + k * 32),
+                                             idesc, 1u);
+                            umma_commit<CG>(&tl.empty[st_h]);
+                            umma_commit<CG>(&tl.empty[st_l]);
+                        }
+                    }
+                    for (int kb = 0; ok && w.resp && kb < nkb; ++kb) {
                         if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
                             rc.abort = 1;
                             ok = false;
