@@ -20,8 +20,13 @@
 // (true X = stored X + c I).
 //
 // Kernel structure (one cooperative persistent launch for the whole chain):
-//   warp 0      TMA producer: 2-D tiled bulk copies (128B swizzle) of a 128 x 64
-//               A block and a 256 x 64 B block per stage into a 4-stage ring.
+//   warp 0      TMA producer: 2-D tiled bulk copies (128B swizzle) into a ring of
+//               stages of one A block (this CTA's rows) and one B block; a square
+//               tile takes each K block in two stages, (hi, hi) and (lo, lo), a
+//               response tile in four, (X hi, Y hi), (X lo, Y lo), (Y hi, X hi),
+//               (Y lo, X lo).  The tensor cores' FP32 accumulator truncates once per
+//               MMA instruction; the small cross products of each K block are issued
+//               before its hi x hi product.
 //   warp 1      tcgen05.mma issuer (one thread): M=128, N=256, K=16 per
 //               instruction, FP32 accumulator in TMEM, double-buffered (2 x 256
 //               columns) so the epilogue of tile t overlaps the MMAs of t+1.
@@ -32,8 +37,8 @@
 //               operands written for the tile and its mirror (only tiles with rows <=
 //               columns are computed), compensated FP64 partials of Tr X and ||X||_F^2.
 // Between layers: grid barrier, then every CTA takes the same layer decision.
-// The response / adjoint stream reuses the same machinery with six K segments:
-// (C + C^T)[i,j] = sum_k X[i,k] Y[j,k] + Y[i,k] X[j,k] for symmetric X and Y.
+// The response / adjoint stream reuses the same machinery with six products per K
+// block: (C + C^T)[i,j] = sum_k X[i,k] Y[j,k] + Y[i,k] X[j,k] for symmetric X and Y.
 #include "device_common.cuh"
 
 namespace sp2i {
@@ -274,32 +279,6 @@ __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams
     return w;
 }
 
-// Tensor maps of the K segment visited at position `pos`: returns the A and B maps
-// (per slot, maps op0, op1, op2 = hi, hi, lo).
-// The tensor cores' FP32 accumulator truncates once per MMA instruction, by up to
-// one unit in the last place of its current value.  The small cross-term segments
-// (hi x lo, lo x hi, 2^-11 of the result) are therefore accumulated first, while
-// the accumulator is still small, and the dominant hi x hi segment last.
-__device__ __forceinline__ void segment_maps(const InstDesc &d, const TileWork &w, int pos, const CUtensorMap *&am,
-                                             const CUtensorMap *&bm) {
-    const int s = w.resp ? (int)((0x305421u >> (4 * pos)) & 0xFu)   // segments 1, 2, 4, 5, then 0, 3
-                         : (int)((0x021u >> (4 * pos)) & 0xFu);     // segments 1, 2, then 0
-    const CUtensorMap *X3 = d.xmap + w.xslot * 3;
-    if (!w.resp) {
-        am = X3 + s;                           // hi, hi, lo
-        bm = X3 + (s == 1 ? 2 : 1);            // hi, lo, hi
-    } else {
-        const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
-        if (s < 3) {
-            am = X3 + s;                       // X hi, hi, lo
-            bm = Y3 + (s == 1 ? 2 : 1);        // Y hi, lo, hi
-        } else {
-            am = Y3 + (s == 4 ? 2 : 1);        // Y hi, lo, hi
-            bm = X3 + (s - 3);                 // X hi, hi, lo
-        }
-    }
-}
-
 template <int PREC, int CG>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_constant__ RunParams p) {
     using C = Cfg<CG>;
@@ -400,22 +379,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     const TileWork w = describe(rc, p, g);
                     const InstDesc &d = p.inst[w.inst];
                     const int nkb = d.np / TC_BK;
-                    const int nseg = w.resp ? 6 : 3;
                     const int row_a = w.bi * C::TILE_M + (int)rank * 128;
                     const int row_b = w.bj * TC_BN + (CG == 2 ? (int)rank * 128 : 0);
                     // Square tiles: each K block in two consecutive ring slots, (hi, hi) then
                     // (lo, lo), which feed all three products.  Response tiles: the six
                     // segments one after another, one K block per slot.
-                    const int nslot = w.resp ? nseg * nkb : 2 * nkb;
+                    const int nslot = (w.resp ? 4 : 2) * nkb;
+                    const CUtensorMap *X3 = d.xmap + w.xslot * 3;   // maps hi, hi, lo
                     for (int kb = 0; kb < nslot; ++kb) {
                         int kx;
                         const CUtensorMap *am, *bm;
                         if (w.resp) {
-                            const int s = kb / nkb;
-                            kx = (kb - s * nkb) * TC_BK;
-                            segment_maps(d, w, s, am, bm);
+                            // Response / adjoint tiles: per K block (X hi, Y hi), (X lo, Y lo),
+                            // (Y hi, X hi), (Y lo, X lo) -- rows bi on the A side, rows bj on the B
+                            // side -- feeding X Y^T and Y X^T.
+                            const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
+                            const int q = kb & 3;
+                            kx = (kb >> 2) * TC_BK;
+                            const CUtensorMap *xm = (q & 1) ? X3 + 2 : X3 + 1, *ym = (q & 1) ? Y3 + 2 : Y3 + 1;
+                            am = (q < 2) ? xm : ym;
+                            bm = (q < 2) ? ym : xm;
                         } else {
-                            const CUtensorMap *X3 = d.xmap + w.xslot * 3;   // maps hi, hi, lo
                             kx = (kb >> 1) * TC_BK;
                             am = bm = (kb & 1) ? X3 + 2 : X3 + 1;
                         }
@@ -451,7 +435,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 for (int g = cluster_id; g < rc.total && !*abort; g += nclusters) {
                     const TileWork w = describe(rc, p, g);
                     const InstDesc &d = p.inst[w.inst];
-                    const int nkb = (d.np / TC_BK) * (w.resp ? 6 : 3);
                     if (!mbar_wait(&tl.tempty[acc], acc_phase ^ 1u, abort, p.timeout_ns, p.err)) {
                         rc.abort = 1;
                         break;
@@ -503,24 +486,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             umma_commit<CG>(&tl.empty[st_l]);
                         }
                     }
-                    for (int kb = 0; ok && w.resp && kb < nkb; ++kb) {
-                        if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                            rc.abort = 1;
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t sa = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
-                        const uint32_t sb = sa + C::A_BYTES;
+                    if (w.resp) {
+                        // Response: per K block the slots (X hi, Y hi), (X lo, Y lo) for X Y^T,
+                        // released as soon as those products are issued, then (Y hi, X hi),
+                        // (Y lo, X lo) for Y X^T; cross terms before hi x hi in each.
+                        for (int kb = 0; ok && kb < d.np / TC_BK; ++kb) {
+#pragma unroll 1
+                            for (int pr = 0; pr < 2; ++pr) {
+                                const uint32_t st_h = stage;
+                                if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                                    rc.abort = 1;
+                                    ok = false;
+                                    break;
+                                }
+                                const uint32_t sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                                if (++stage == C::STAGES) {
+                                    stage = 0;
+                                    phase ^= 1u;
+                                }
+                                const uint32_t st_l = stage;
+                                if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                                    rc.abort = 1;
+                                    ok = false;
+                                    break;
+                                }
+                                const uint32_t sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                                if (++stage == C::STAGES) {
+                                    stage = 0;
+                                    phase ^= 1u;
+                                }
+                                tc_fence_after();
 #pragma unroll
-                        for (int k = 0; k < TC_BK / 16; ++k) {
-                            umma_f16<CG>(d_tmem, sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
-                                         (kb | k) != 0 ? 1u : 0u);
-                        }
-                        umma_commit<CG>(&tl.empty[stage]);
-                        if (++stage == C::STAGES) {
-                            stage = 0;
-                            phase ^= 1u;
+                                for (int k = 0; k < TC_BK / 16; ++k)   // A hi x B lo
+                                    umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32),
+                                                 sdesc_sw128(sl + C::A_BYTES + k * 32), idesc,
+                                                 (kb | pr | k) != 0 ? 1u : 0u);
+#pragma unroll
+                                for (int k = 0; k < TC_BK / 16; ++k)   // A lo x B hi
+                                    umma_f16<CG>(d_tmem, sdesc_sw128(sl + k * 32),
+                                                 sdesc_sw128(sh + C::A_BYTES + k * 32), idesc, 1u);
+#pragma unroll
+                                for (int k = 0; k < TC_BK / 16; ++k)   // A hi x B hi
+                                    umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32),
+                                                 sdesc_sw128(sh + C::A_BYTES + k * 32), idesc, 1u);
+                                umma_commit<CG>(&tl.empty[st_h]);
+                                umma_commit<CG>(&tl.empty[st_l]);
+                            }
                         }
                     }
                     umma_commit<CG>(&tl.tfull[acc]);
