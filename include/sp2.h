@@ -118,7 +118,9 @@ typedef struct {
     int test_hook;        /* 0 in normal use; 1 = CTA 0 withholds its first grid-barrier arrival, so
                              the barrier wait must run out (tests the timeout path); 2 = every
                              device allocation the call makes reports failure (host-side
-                             injection; tests the SP2_ERR_NOMEM path) */
+                             injection; tests the SP2_ERR_NOMEM path); 3 = as 1 but in CTA-pair
+                             launches only (a pair that never becomes resident; tests the retry
+                             described under cta_group) */
     double eps_min;
     double eps_max;
     int profile;          /* 1 = record per-phase device times into sp2_stats.phase_ms */
@@ -126,8 +128,10 @@ typedef struct {
                              tile (cooperative launch), 2 = a CTA pair per 256 x 256 tile
                              (M = 256 MMAs; a cluster launch sized to the pairs the device
                              holds at once: work running concurrently on the same GPU can
-                             deny that residency, and the call then ends with
-                             SP2_ERR_TIMEOUT after timeout_ms) */
+                             deny that residency, and the grid barrier then runs out after
+                             timeout_ms -- with cta_group = 0 the call is then retried once
+                             with single-CTA tiles, with cta_group = 2 it returns
+                             SP2_ERR_TIMEOUT; batch plans do not retry) */
     int accelerate;       /* 1 = accelerated chain from an estimated interval [eps_homo, eps_lumo]
                              between the highest occupied and lowest unoccupied eigenvalue
                              (section "GPU and tensor core performance" notes the saving of up

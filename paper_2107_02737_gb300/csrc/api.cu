@@ -599,7 +599,8 @@ sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
     rp.mode = pl.mode;
     rp.precision = pl.precision;
     rp.max_layers = P.o.max_layers;
-    rp.test_hook = P.o.test_hook == 1 ? 1 : 0;  // the device sees only the barrier hook
+    // Device hook: CTA 0 withholds its first barrier arrival (test_hook 1, or 3 in a CTA-pair launch).
+    rp.test_hook = (P.o.test_hook == 1 || (P.o.test_hook == 3 && pl.path == PATH_TC && pl.cg == 2)) ? 1 : 0;
     if (ev) CK(cudaEventRecord(ev[1], s));
     CK(pl.path == PATH_TC ? launch_tc_persistent(rp, pl.cg, P.grid, s) : launch_simt_persistent(rp, P.grid, s));
     if (ev) CK(cudaEventRecord(ev[2], s));
@@ -634,13 +635,15 @@ sp2_status collect(Prepared &P, cudaStream_t s, const float *ph) {
     return (sp2_status)worst;
 }
 
-sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws_bytes, cudaStream_t s) {
+sp2_status run_plan_once(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws_bytes, cudaStream_t s,
+                         int *used_cg) {
     const int B = (int)pl.inst.size();
     if (B == 0) return SP2_OK;
     Prepared P;
     P.pl = pl;
     sp2_status r = choose_launch(P.pl, o.cta_group, P.grid);
     if (r != SP2_OK) return r;
+    *used_cg = (P.pl.path == PATH_TC) ? P.pl.cg : 0;
     Arena arena(s);
     arena.fail = (o.test_hook == 2);
     const size_t need = plan_bytes(P.pl);
@@ -679,6 +682,22 @@ sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws
     return r;
 }
 
+// A CTA-pair launch relies on every pair being resident at once (it is a cluster
+// launch, not a cooperative one); work running concurrently on the same GPU can
+// deny that, and the grid barrier then runs out of time.  When the tile shape was
+// left to the library, the call is retried once with single-CTA tiles, whose
+// cooperative launch guarantees co-residency.
+sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws_bytes, cudaStream_t s) {
+    int used_cg = 0;
+    sp2_status r = run_plan_once(pl, tol, o, ws, ws_bytes, s, &used_cg);
+    if (r == SP2_ERR_TIMEOUT && used_cg == 2 && o.cta_group == 0 && o.test_hook != 1) {
+        sp2_opts o1 = o;
+        o1.cta_group = 1;
+        r = run_plan_once(pl, tol, o1, ws, ws_bytes, s, &used_cg);
+    }
+    return r;
+}
+
 bool integral_occ(double n_occ, int n) {
     return std::isfinite(n_occ) && n_occ >= 0.0 && n_occ <= (double)n && std::floor(n_occ) == n_occ;
 }
@@ -688,7 +707,7 @@ sp2_status check_opts(const sp2_opts &o) {
     if (o.max_layers < 1 || o.max_layers > SP2_MAX_LAYERS_LIMIT) return SP2_ERR_ARG;
     if (!(o.timeout_ms > 0.0)) return SP2_ERR_ARG;
     if (o.user_bounds && !(o.eps_max > o.eps_min)) return SP2_ERR_ARG;
-    if (o.test_hook < 0 || o.test_hook > 2) return SP2_ERR_ARG;
+    if (o.test_hook < 0 || o.test_hook > 3) return SP2_ERR_ARG;
     if (o.profile < 0 || o.profile > 1) return SP2_ERR_ARG;
     if (o.cta_group < 0 || o.cta_group > 2) return SP2_ERR_ARG;
     if (o.accelerate < 0 || o.accelerate > 1) return SP2_ERR_ARG;

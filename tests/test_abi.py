@@ -68,6 +68,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
     o = sp2.make_opts(bounds=(1.0, 0.0))
     assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
+    o = sp2.make_opts()
+    o.test_hook = 4
+    assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG
     for stride in (-2, 201):
         o = sp2.make_opts(checkpoint_stride=stride)
         assert _call_density(lib, 8, 4, opts=ctypes.byref(o)) == sp2.ERR_ARG

@@ -95,3 +95,24 @@ def test_allocation_failure_returns_nomem(precision):
     # and nothing is left behind: a normal call still works
     D2, _ = sp2.density(H, 128, precision=precision)
     assert torch.equal(D2, D)
+
+
+def test_pair_residency_timeout_falls_back_to_single_cta():
+    """A CTA pair that never becomes resident (test_hook = 3 withholds a barrier arrival in
+    pair launches only): with the tile shape left to the library the call retries with
+    single-CTA tiles and succeeds; forced to pairs it reports the timeout."""
+    import ctypes
+    n = 256
+    ham = inputs.gapped_random(n, 128, np.random.default_rng(6))
+    H = dev(ham.H)
+    D = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    o = sp2.make_opts("fp16", timeout_ms=100.0)
+    o.test_hook = 3
+    st = sp2._new_stats()
+    s = sp2.load().sp2_density(ctypes.c_void_p(H.data_ptr()), n, 128.0, 1e-6, ctypes.c_void_p(D.data_ptr()),
+                               ctypes.byref(st), ctypes.byref(o), None, 0,
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert s == sp2.OK and st.cta_group == 1
+    assert fro_err(host(D), odens.density_matrix(ham.H, 128)) <= TOL_D["fp16"]
+    o.cta_group = 2
+    assert _raw_density(H.data_ptr(), n, 128, D, o) == sp2.ERR_TIMEOUT
