@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode
 // memory: each tile is written to (ti, tj) and, transposed, to (tj, ti), both
 // with coalesced rows.  H is symmetric, so Tr[D H] is summed over the lower
 // triangle with off-diagonal weight 2.
-__global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mode) {
+// Eight blocks per SM (32 registers per thread at most): the 1024 blocks then run as one wave.
+__global__ void __launch_bounds__(AUX_THREADS, 8) k_finalize(InstDesc *inst, int mode) {
     __shared__ float sx[32][33], sy[32][33];
     const InstDesc &d = inst[blockIdx.y];
     if (blockIdx.x >= d.fin_blocks) return;
@@ -361,8 +362,9 @@ __global__ void __launch_bounds__(AUX_THREADS) k_finalize(InstDesc *inst, int mo
     const int nt = (n + 31) / 32;
     const long long ntiles = (long long)nt * (nt + 1) / 2;
     for (long long k = blockIdx.x; k < ntiles; k += d.fin_blocks) {
-        // k -> (ti, tj) with tj <= ti, row-major over the lower triangle of tiles
-        int ti = (int)((sqrt(8.0 * (double)k + 1.0) - 1.0) * 0.5);
+        // k -> (ti, tj) with tj <= ti, row-major over the lower triangle of tiles: an FP32
+        // root (FP64 is slow on this GPU) corrected to the exact integer below
+        int ti = (int)((sqrtf(8.0f * (float)k + 1.0f) - 1.0f) * 0.5f);
         while ((long long)(ti + 1) * (ti + 2) / 2 <= k) ++ti;
         while ((long long)ti * (ti + 1) / 2 > k) --ti;
         const int tj = (int)(k - (long long)ti * (ti + 1) / 2);
