@@ -17,18 +17,23 @@
  *  - Matrices are dense, row-major, N x N, with leading dimension N.
  *  - Matrix pointers may be device pointers or host pointers (pageable or
  *    pinned); the library detects which and stages host data through device
- *    memory.  The caller owns every buffer it passes; the library frees none.
+ *    memory.  Pinned (page-locked, mapped) host memory is accessed in place
+ *    across the host link: of H (and of a response's H1) only the lower
+ *    triangle, diagonal included, is read, and D (D1, dH) is written there
+ *    directly by the output kernel.  Pageable host matrices are copied whole.
+ *    The caller owns every buffer it passes; the library frees none.
  *  - H must be symmetric (bit-exactly, as produced by (A + A^T)/2); the result
- *    for an asymmetric H is unspecified but finite.
+ *    for an asymmetric H is unspecified but finite (with pinned H it is that
+ *    of the symmetric matrix with H's lower triangle).
  *  - `n_occ` must be an integer value in [0, N].  n_occ = 0 gives D = 0 and
  *    n_occ = N gives D = I without layers.
  *  - `workspace` may be NULL, in which case the call allocates device memory
  *    and frees it before returning; otherwise it must be a device pointer of
  *    at least the size the matching *_workspace_bytes function returns,
- *    256-byte aligned.  Host-resident matrices are staged in the workspace
- *    beyond that size when it is large enough (8 bytes per FP64 and 4 per FP32
- *    element, each piece rounded up to 256 bytes), else in memory the call
- *    allocates and frees.
+ *    256-byte aligned.  Host-resident inputs, and pageable host outputs, are
+ *    staged in the workspace beyond that size when it is large enough (8 bytes
+ *    per FP64 and 4 per FP32 element, each piece rounded up to 256 bytes), else
+ *    in memory the call allocates and frees.
  *  - Calls are stream-ordered on `stream` (a cudaStream_t; NULL = legacy
  *    default stream) and synchronise that stream before returning, because
  *    the status and the statistics are read back to the host.

@@ -22,7 +22,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsp2.so")
-SOURCES = ["aux_kernels.cu", "simt_kernel.cu", "tc_kernel.cu", "api.cu", "noalloc.cu", "fp64_ext.cu"]
+SOURCES = ["aux_kernels.cu", "simt_kernel.cu", "tc_kernel.cu", "api.cu", "noalloc.cu", "fp64_ext.cu",
+           "host_link.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "host_link.h"
 
 using namespace sp2i;
 
@@ -494,8 +495,12 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
 
     // Host-resident inputs and outputs go through device memory: the tail of
     // the caller's workspace when it has room, else a stream-ordered allocation
-    // freed before the call returns.
+    // freed before the call returns.  Page-locked host memory is used in place
+    // across the host link: symmetric inputs (H, and H1 of a response) cross
+    // it as their lower triangle only, and D / D1 are written to it directly
+    // by the output kernel.  Pageable memory is copied whole.
     const size_t ws_end = ws_bytes;
+    bool staging_err = false;
     auto staging = [&](size_t bytes) -> void * {
         const size_t start = (c.off + 255) & ~(size_t)255;
         if (ws_end && start + bytes <= ws_end) return c.take(bytes);
@@ -509,37 +514,48 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         const bool hX0 = sp.X0 && !is_device_ptr(sp.X0), hD = sp.D && !is_device_ptr(sp.D);
         const bool hD1 = sp.D1 && !is_device_ptr(sp.D1);
         if (!staging_ok && (hH || hH1 || hX0 || hD || hD1)) return SP2_ERR_ARG;
+        auto stage_input = [&](const double *src, bool symmetric) -> double * {
+            double *t = (double *)staging(nn * 8);
+            if (!t) return nullptr;
+            const void *m = symmetric ? mapped_host_ptr(src) : nullptr;
+            const cudaError_t e = m ? launch_stage_lower((const double *)m, t, sp.n, s)
+                                    : cudaMemcpyAsync(t, src, nn * 8, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                staging_err = true;
+            }
+            return t;
+        };
         if (hH) {
-            double *t = (double *)staging(nn * 8);
-            if (!t) return SP2_ERR_NOMEM;
-            CK(cudaMemcpyAsync(t, sp.H, nn * 8, cudaMemcpyHostToDevice, s));
-            d.H = t;
+            d.H = stage_input(sp.H, true);
+            if (!d.H) return SP2_ERR_NOMEM;
         }
-        if (hH1) {
-            double *t = (double *)staging(nn * 8);
-            if (!t) return SP2_ERR_NOMEM;
-            CK(cudaMemcpyAsync(t, sp.H1, nn * 8, cudaMemcpyHostToDevice, s));
-            d.H1 = t;
+        if (hH1) {  // the adjoint's weight G need not be symmetric
+            d.H1 = stage_input(sp.H1, pl.mode == MODE_RESPONSE);
+            if (!d.H1) return SP2_ERR_NOMEM;
         }
+        if (staging_err) return SP2_ERR_CUDA;
         if (hX0) {
             float *t = (float *)staging(nn * 4);
             if (!t) return SP2_ERR_NOMEM;
             CK(cudaMemcpyAsync(t, sp.X0, nn * 4, cudaMemcpyHostToDevice, s));
             sp.X0 = t;
         }
-        if (hD) {
+        auto stage_output = [&](float *dst) -> float * {
+            if (const void *m = mapped_host_ptr(dst)) return (float *)m;  // written across the link
             float *t = (float *)staging(nn * 4);
-            if (!t) return SP2_ERR_NOMEM;
-            P.copy_back.push_back({sp.D, t});
+            if (!t) return nullptr;
+            P.copy_back.push_back({dst, t});
             P.copy_back_n.push_back(nn);
-            d.out = t;
+            return t;
+        };
+        if (hD) {
+            d.out = stage_output(sp.D);
+            if (!d.out) return SP2_ERR_NOMEM;
         }
         if (hD1) {
-            float *t = (float *)staging(nn * 4);
-            if (!t) return SP2_ERR_NOMEM;
-            P.copy_back.push_back({sp.D1, t});
-            P.copy_back_n.push_back(nn);
-            d.out1 = t;
+            d.out1 = stage_output(sp.D1);
+            if (!d.out1) return SP2_ERR_NOMEM;
         }
     }
 

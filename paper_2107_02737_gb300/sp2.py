@@ -211,6 +211,13 @@ def _f64(t: torch.Tensor, name: str) -> torch.Tensor:
     return t.contiguous()
 
 
+def _empty_like_host(H: torch.Tensor, n: int) -> torch.Tensor:
+    """An N x N FP32 result on H's device; page-locked when H is, so that the
+    library writes it in place across the host link instead of copying it."""
+    pinned = H.device.type == "cpu" and H.is_pinned()
+    return torch.empty((n, n), dtype=torch.float32, device=H.device, pin_memory=pinned)
+
+
 def _ws_args(workspace: Optional[torch.Tensor]):
     if workspace is None:
         return None, 0
@@ -242,7 +249,7 @@ def density(H: torch.Tensor, n_occ: int, tol: float = 1e-6, precision: str = "fp
     """
     H = _f64(H, "H")
     n = _square(H, "H")
-    D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=H.device)
+    D = out if out is not None else _empty_like_host(H, n)
     st = _new_stats()
     o = make_opts(precision, max_layers, timeout_ms, bounds, profile, cta_group, gap)
     ws, wsb = _ws_args(workspace)
@@ -260,8 +267,8 @@ def response(H: torch.Tensor, H1: torch.Tensor, n_occ: int, tol: float = 1e-6, p
     (with ``fwd`` the forward run's layer signs and expansions are replayed instead)."""
     H, H1 = _f64(H, "H"), _f64(H1, "H1")
     n = _square(H, "H")
-    D = torch.empty((n, n), dtype=torch.float32, device=H.device)
-    D1 = torch.empty((n, n), dtype=torch.float32, device=H.device)
+    D = _empty_like_host(H, n)
+    D1 = _empty_like_host(H, n)
     st = _new_stats()
     o = make_opts(precision, max_layers, timeout_ms, bounds, cta_group=cta_group, gap=gap)
     ws, wsb = _ws_args(workspace)
@@ -283,8 +290,8 @@ def adjoint(H: torch.Tensor, G: torch.Tensor, n_occ: int, tol: float = 1e-6, pre
     reverse sweep (same result bit for bit, less memory); -1 picks s."""
     H, G = _f64(H, "H"), _f64(G, "G")
     n = _square(H, "H")
-    D = torch.empty((n, n), dtype=torch.float32, device=H.device)
-    dH = torch.empty((n, n), dtype=torch.float32, device=H.device)
+    D = _empty_like_host(H, n)
+    dH = _empty_like_host(H, n)
     st = _new_stats()
     o = make_opts(precision, max_layers, timeout_ms, gap=gap, checkpoint_stride=checkpoint_stride)
     ws, wsb = _ws_args(workspace)
@@ -304,8 +311,7 @@ def density_batched(Hs: Sequence[torch.Tensor], n_occs: Sequence[int], tol: floa
     B = len(Hs)
     Hs = [_f64(h, f"H[{i}]") for i, h in enumerate(Hs)]
     ns = [_square(h, f"H[{i}]") for i, h in enumerate(Hs)]
-    Ds = list(outs) if outs is not None else [torch.empty((n, n), dtype=torch.float32, device=h.device)
-                                                for n, h in zip(ns, Hs)]
+    Ds = list(outs) if outs is not None else [_empty_like_host(h, n) for n, h in zip(ns, Hs)]
     sts = (Stats * B)()
     keep = []
     for b in range(B):
