@@ -1,6 +1,6 @@
 """Timing of the secondary workloads (one JSON line each).
 
-    python -m paper_2107_02737_gb300.measure --workload batched|response|adjoint|md
+    python -m paper_2107_02737_gb300.measure --workload batched|response|adjoint|md|refined|accel|host
 
 * ``batched``  — 64 gapped Hamiltonians of N in {128, ..., 2048}, BF16 split, one
   grouped persistent launch per step; effective TFLOP/s = sum_i L_i 2 N_i^3 / t.
@@ -14,9 +14,13 @@
   emulated on the tensor cores); reports the added time and the trace.
 * ``accel``    — the N = 8192 chain, plain and accelerated from the generator's exact
   HOMO / LUMO (and from an interval four gaps wide around it); ms to D and layers.
+* ``host``     — the N = 8192 chain called with host-resident H and D: page-locked
+  (H read in place as its lower triangle, D written in place) and pageable (both
+  copied whole), host wall time per call against the device-resident call.
 
-Device time with CUDA events around each call, after warm-up; inputs resident on
-the device.  These are reports, not the headline benchmark (bench.py).
+Device time with CUDA events around each call, after warm-up, inputs resident on
+the device (``host``: host wall time of each synchronous call).  These are
+reports, not the headline benchmark (bench.py).
 """
 from __future__ import annotations
 
@@ -128,9 +132,36 @@ def accel(steps, warmup, n=8192, precision="fp16"):
     return out
 
 
+def host(steps, warmup, n=8192, precision="fp16"):
+    import time
+
+    ham = inputs.water_like_workload(n)
+    Hd = torch.tensor(ham.H, device="cuda")
+    dev_ms, (Dd, r0) = _time(lambda: sp2.density(Hd, ham.n_occ, precision=precision), steps, warmup)
+    ref = Dd.cpu()
+    out = {"workload": f"host round trip N={n}", "precision": precision, "layers": r0.layers,
+           "device_resident_ms": dev_ms}
+    for name, pin in [("page_locked", True), ("pageable", False)]:
+        H = torch.from_numpy(ham.H)
+        D = torch.empty((n, n), dtype=torch.float32)
+        if pin:
+            H, D = H.pin_memory(), D.pin_memory()
+        for _ in range(warmup):
+            sp2.density(H, ham.n_occ, precision=precision, out=D)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            _, r = sp2.density(H, ham.n_occ, precision=precision, out=D)
+        ms = (time.perf_counter() - t0) * 1e3 / steps
+        h2d = (n * (n + 1) // 2 if pin else n * n) * 8
+        out[name] = {"ms_per_call": ms, "added_ms": ms - dev_ms, "h2d_bytes": h2d, "d2h_bytes": n * n * 4,
+                     "effective_tflops": r.layers * 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                     "equal_to_device_result": bool(torch.equal(D, ref))}
+    return out
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", choices=["batched", "response", "adjoint", "md", "refined", "accel"],
+    ap.add_argument("--workload", choices=["batched", "response", "adjoint", "md", "refined", "accel", "host"],
                     required=True)
     ap.add_argument("--accelerate", action="store_true", help="md: reuse HOMO / LUMO estimates step to step")
     ap.add_argument("--steps", type=int, default=5)
@@ -147,6 +178,8 @@ def main(argv=None) -> int:
         out = refined(a.steps, a.warmup, a.n or 8192)
     elif a.workload == "accel":
         out = accel(a.steps, a.warmup, a.n or 8192)
+    elif a.workload == "host":
+        out = host(a.steps, a.warmup, a.n or 8192)
     else:
         return md.main(["--n", str(a.n or 12288), "--steps", str(a.steps)] + (["--accelerate"] if a.accelerate else []))
     print(json.dumps(out))
