@@ -137,7 +137,12 @@ def host(steps, warmup, n=8192, precision="fp16"):
 
     ham = inputs.water_like_workload(n)
     Hd = torch.tensor(ham.H, device="cuda")
-    dev_ms, (Dd, r0) = _time(lambda: sp2.density(Hd, ham.n_occ, precision=precision), steps, warmup)
+    # Caller workspaces, as a repeated caller passes them: the solve's own, and with
+    # room after it for staging host matrices (8 bytes per H and 4 per D element).
+    wsb = sp2.workspace_bytes(n, "density", precision)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    ws_host = torch.empty(wsb + n * n * 12 + 4096, dtype=torch.uint8, device="cuda")
+    dev_ms, (Dd, r0) = _time(lambda: sp2.density(Hd, ham.n_occ, precision=precision, workspace=ws), steps, warmup)
     ref = Dd.cpu()
     out = {"workload": f"host round trip N={n}", "precision": precision, "layers": r0.layers,
            "device_resident_ms": dev_ms}
@@ -147,10 +152,10 @@ def host(steps, warmup, n=8192, precision="fp16"):
         if pin:
             H, D = H.pin_memory(), D.pin_memory()
         for _ in range(warmup):
-            sp2.density(H, ham.n_occ, precision=precision, out=D)
+            sp2.density(H, ham.n_occ, precision=precision, out=D, workspace=ws_host)
         t0 = time.perf_counter()
         for _ in range(steps):
-            _, r = sp2.density(H, ham.n_occ, precision=precision, out=D)
+            _, r = sp2.density(H, ham.n_occ, precision=precision, out=D, workspace=ws_host)
         ms = (time.perf_counter() - t0) * 1e3 / steps
         h2d = (n * (n + 1) // 2 if pin else n * n) * 8
         out[name] = {"ms_per_call": ms, "added_ms": ms - dev_ms, "h2d_bytes": h2d, "d2h_bytes": n * n * 4,
