@@ -46,7 +46,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    # --size is the same option under a name that torchrun's own parser cannot take for one of its
+    # options (it rejects --n as an ambiguous abbreviation).
+    ap.add_argument("--n", "--size", dest="n", type=int, default=N_DEFAULT, help="matrix size N")
     ap.add_argument("--precision", choices=["fp16", "bf16"], default="fp16")
     ap.add_argument("--fp32-steps", type=int, default=2, help="steps of the FP32 CUDA-core comparator")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0, help="CPU seconds for the oracle sample")
@@ -163,6 +165,19 @@ def profiled_traffic(n, layers, precision):
     return None
 
 
+def workload_config(n, n_occ):
+    """The config keys both arms share: the workload, named by what it is."""
+    return {"workload": f"water-like banded tight-binding H, N={n}, n_occ={n_occ}, gap>=0.05 (seeded)",
+            "n": n, "n_occ": n_occ}
+
+
+def l2_note(n):
+    """Timing hygiene: whether the inputs exceed the 129 MB L2 (no flush between steps)."""
+    h_mb, op_mb = n * n * 8 / 1e6, n * n * 4 / 1e6
+    big = "inputs larger than L2" if min(h_mb, op_mb) > 129 else "inputs NOT larger than L2"
+    return f"{big} (H is {h_mb:.0f} MB FP64; split operands {op_mb:.0f} MB per layer; L2 129 MB)"
+
+
 def eff_tflops(layers, n, ms):
     return layers * 2.0 * float(n) ** 3 / (ms * 1e-3) / 1e12
 
@@ -192,8 +207,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"water-like banded tight-binding H, N={n}, n_occ={ham.n_occ}, gap>=0.05",
-                       "n": n, "n_occ": ham.n_occ, "step": "one FP64 layer of the oracle SP2 chain (DGEMM)"},
+            "config": {**workload_config(n, ham.n_occ), "step": "one FP64 layer of the oracle SP2 chain (DGEMM)"},
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} FP64 SP2 layers at N={n}, one per step"},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -201,7 +215,7 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline_leg(ham, gpu_choices, D_gpu, budget_s):  # noqa: ARG001 (D_gpu kept for symmetry)
+def cpu_baseline_leg(ham, gpu_choices, budget_s):
     """The FP64 oracle on this host: timed chain sample, and the accuracy reference."""
     from oracle import density as odens
     from oracle import sp2 as osp2
@@ -325,9 +339,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f16" if args.precision == "fp16" else "bf16", "data": "synthetic",
-        "config": {"workload": f"water-like banded tight-binding H, N={n}, n_occ={n_occ}, gap>=0.05 (seeded)",
-                   "n": n, "n_occ": n_occ, "precision": f"split {args.precision} hi/lo, FP32 accumulation",
-                   "l2": "inputs larger than L2 (H is 537 MB FP64; split operands 402 MB)",
+        "config": {**workload_config(n, n_occ), "precision": f"split {args.precision} hi/lo, FP32 accumulation",
+                   "l2": l2_note(n),
                    "parallelism": "replicas" if world > 1 else "single", "kernel_sha": kernel_source_sha()},
         "layers": L, "stop_reason": res.stop_reason, "cta_group": res.cta_group,
         "accuracy": {"fro_err_vs_fp64_per_sqrtN": None, "idempotency_fro": idem, "trace_err": res.trace_D - n_occ,
@@ -348,7 +361,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
     }
     if not args.no_cpu_baseline:
-        cpu, D_ref = cpu_baseline_leg(ham, res.choices, D_host, args.cpu_budget_s)
+        cpu, D_ref = cpu_baseline_leg(ham, res.choices, args.cpu_budget_s)
         line["cpu_baseline"] = cpu
         line["accuracy"]["fro_err_vs_fp64_per_sqrtN"] = float(np.linalg.norm(D_host - D_ref) / np.sqrt(n))
         D32_host = D32.cpu().double().numpy()
