@@ -5,10 +5,9 @@
 //               layers keep its lower triangle and diagonal current (the next layer
 //               reads (c, r) for its tiles' r <= c); the output kernel mirrors it.
 //   xop slots   split operands of X_n, two 16-bit matrices per slot, hi and lo
-//               (FP16 lo stored times 2^11), so that the square is one K-loop of
-//               length 3*np over A = [hi | hi | lo] and B = [hi | lo | hi] (Eq. activ:
-//               A + B + B^T with the lo*lo term dropped, all three products in one
-//               FP32 accumulator).
+//               (FP16: both stored times 2^11), from which each K block of the
+//               square issues hi*lo, lo*hi and hi*hi into one FP32 accumulator
+//               (Eq. activ: A + B + B^T with the lo*lo term dropped).
 //   yf[2], yop  the response / adjoint stream (FP32 master + hi, lo).
 //   adjoint with checkpoint stride s: operand slots 0..K-1 hold X_0, X_s, ...,
 //               X_{(K-1)s} (with FP32 masters in ckf), slots K..K+s-2 the others

@@ -4,8 +4,8 @@
 // dual 16-bit representation X = X^(0) + X^(1) as X^(0)X^(0) + X^(0)X^(1) +
 // X^(1)X^(0) (the paper's A + B + B^T; the X^(1)X^(1) term is dropped), all
 // three products accumulated in one FP32 accumulator in tensor memory:
-//   S[i,j] = sum over one K-loop of length 3*np of A[i,k] * B[j,k],
-//   A = [hi | hi | lo], B = [hi | lo | hi]   (rows of X; X is symmetric).
+//   S[i,j] = sum_k hi[i,k] lo[j,k] + lo[i,k] hi[j,k] + hi[i,k] hi[j,k]
+// (rows of X; X is symmetric), all three issued from the same staged K block.
 // FP16 stores both parts times 2^11 (so lo stays in FP16's normal range): every
 // product carries 2^22, removed in the epilogue.  BF16 needs no scaling.
 //
@@ -19,7 +19,8 @@
 // reduced in FP64) and carried to the next layer as a scalar offset c
 // (true X = stored X + c I).
 //
-// Kernel structure (one cooperative persistent launch for the whole chain):
+// Kernel structure (one persistent launch for the whole chain: cooperative for
+// single-CTA tiles, a cluster launch sized to the resident pairs for CTA pairs):
 //   warp 0      TMA producer: 2-D tiled bulk copies (128B swizzle) into a ring of
 //               stages of one A block (this CTA's rows) and one B block; a square
 //               tile takes each K block in two stages, (hi, hi) and (lo, lo), a
@@ -228,7 +229,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // ---------------------------------------------------------------------------
 struct TileWork {
     int inst, job, tile, bi, bj;
-    int resp;            // 0: square of X (3 segments), 1: C + C^T of X and Y (6 segments)
+    int resp;            // 0: square of X (three products per K block), 1: C + C^T of X and Y (six)
     int xslot;           // X operand slot
     int ybuf;            // Y input buffer (resp)
     int flip;            // layer choice is 2X - X^2
