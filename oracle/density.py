@@ -112,6 +112,27 @@ def response_from_eigensystem(lam, C, H1, n_occ) -> np.ndarray:
     return C @ (h1 * F) @ C.T
 
 
+def response_rows(lam, C, H1, n_occ: int, rows) -> np.ndarray:
+    """Selected rows of D1 = C (C^T H1 C  o  F) C^T, for very large N.
+
+    F is nonzero only between an occupied state o and an unoccupied state v, where
+    F_ov = F_vo = 1/(eps_o - eps_v).  With C = [C_o  C_v] and W = (C_o^T H1 C_v) o F_ov
+    the formula reads D1 = C_o W C_v^T + C_v W^T C_o^T, of which only the requested
+    rows are formed.
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    rows = np.asarray(rows)
+    f = occupations(len(lam), n_occ)
+    occ, virt = f == 1.0, f == 0.0
+    Co, Cv = C[:, occ], C[:, virt]
+    gap = lam[occ][:, None] - lam[virt][None, :]
+    if np.any(gap == 0):
+        raise ValueError("no gap between occupied and unoccupied eigenvalues")
+    W = (Co.T @ (symmetrise(H1) @ Cv)) / gap
+    return Co[rows] @ W @ Cv.T + Cv[rows] @ W.T @ Co.T
+
+
 def adjoint(H: np.ndarray, G: np.ndarray, n_occ: int) -> np.ndarray:
     """Gradient of Tr[D(H) G] with respect to symmetric H (self-adjoint response)."""
     return response(H, symmetrise(G), n_occ)

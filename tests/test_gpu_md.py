@@ -60,3 +60,24 @@ def test_md_steps_match_oracle(trajectory, fixed, accelerate):
     integ = np.concatenate([[0.0], np.cumsum(0.5 * (F_ref[1:] + F_ref[:-1]))])
     ref_dev = (E_ref - E_ref[0]) - integ
     assert dr["max_abs"] == pytest.approx(float(np.max(np.abs(ref_dev))), abs=2e-4)
+
+
+def test_md_workload_full_size_12288():
+    """The MD workload at its full size (N = 12288): the sequence's first Hamiltonian H_0
+    and its sparse perturbation V through one sp2_response call, as each MD step makes
+    it; sampled rows of D against the generator's eigensystem and of D1 = dD/dH[V]
+    against the perturbation formula."""
+    ham, V = md.trajectory_inputs(12288)
+    n = ham.n
+    D, D1, res = sp2.response(dev(ham.H), dev(V), ham.n_occ, precision="fp16")
+    assert res.converged
+    rows = np.random.default_rng(12).choice(n, size=6, replace=False)
+    idx = torch.tensor(rows, device="cuda")
+    ref = odens.density_rows(ham.eigvecs, ham.n_occ, rows)
+    row_err = float(np.sqrt(np.mean(np.sum((host(D[idx]) - ref) ** 2, axis=1))))
+    ref1 = odens.response_rows(ham.eigvals, ham.eigvecs, V, ham.n_occ, rows)
+    err1 = float(np.linalg.norm(host(D1[idx]) - ref1) / np.linalg.norm(ref1))
+    print(f"\nN=12288 MD start: layers={res.layers} D row err {row_err:.2e}, D1 sampled-row rel err {err1:.2e}, "
+          f"Tr D - n_occ {res.trace_D - ham.n_occ:+.2e}")
+    assert row_err <= TOL_D["fp16"]
+    assert err1 <= 1e-2

@@ -138,6 +138,28 @@ def test_response_matches_central_differences(gapped):
     assert abs(np.trace(D1)) < 1e-12
 
 
+def test_response_rows_match_central_differences_and_closed_form(gapped):
+    """Sampled rows of D1 from the occupied-unoccupied block only: against central
+    differences of the eigendecomposition D, and on a diagonal H against
+    D1_ij = H1_ij (f_i - f_j)/(eps_i - eps_j)."""
+    rng = np.random.default_rng(16)
+    H1 = inputs.symmetric_gaussian(gapped.n, rng) * 0.1
+    rows = [0, 7, 19, 20, 47]
+    h = 1e-5
+    fd = (density.density_matrix(gapped.H + h * H1, gapped.n_occ)
+          - density.density_matrix(gapped.H - h * H1, gapped.n_occ)) / (2 * h)
+    got = density.response_rows(gapped.eigvals, gapped.eigvecs, H1, gapped.n_occ, rows)
+    np.testing.assert_allclose(got, fd[rows], atol=1e-8)
+    eps = np.array([-0.9, -0.4, -0.1, 0.2, 0.5, 0.8])
+    H1d = inputs.symmetric_gaussian(6, rng)
+    f = density.occupations(6, 2)
+    got = density.response_rows(eps, np.eye(6), H1d, 2, [1, 4])
+    for a, i in enumerate([1, 4]):
+        for j in range(6):
+            expect = H1d[i, j] * (f[i] - f[j]) / (eps[i] - eps[j]) if f[i] != f[j] else 0.0
+            assert got[a, j] == pytest.approx(expect, abs=1e-14)
+
+
 def test_adjoint_duality_and_differences(gapped):
     rng = np.random.default_rng(7)
     G = rng.standard_normal((gapped.n, gapped.n))  # not symmetric on purpose
