@@ -72,16 +72,6 @@ DeviceInfo query_device() {
     return di;
 }
 
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 sp2_opts resolve_opts(const sp2_opts *o) {
     sp2_opts r;
     sp2_default_opts(&r);

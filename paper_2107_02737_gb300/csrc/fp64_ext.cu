@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "host_link.h"
 
 namespace {
 
@@ -150,15 +151,6 @@ struct Blas {
 };
 Blas g_blas[64];
 
-bool is_dev(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 // Row-major C = op(A) op(B) for n x n FP64 matrices, FP64 emulated on the tensor cores.
 cublasStatus_t rm_gemm(cublasHandle_t h, int n, bool ta, const double *A, bool tb, const double *B, double *C) {
     const double one = 1.0, zero = 0.0;
@@ -214,14 +206,14 @@ sp2_status run_fp64(const double *H_in, const double *Z_in, int N, double n_occ,
     DevBuf buf(s);
     // Inputs on the device.
     const double *H = H_in;
-    if (!is_dev(H_in)) {
+    if (!is_device_ptr(H_in)) {
         double *t = (double *)buf.get(nn * 8);
         if (!t) return SP2_ERR_NOMEM;
         CKS(cudaMemcpyAsync(t, H_in, nn * 8, cudaMemcpyHostToDevice, s));
         H = t;
     }
     const double *Z = Z_in;
-    if (Z_in && !is_dev(Z_in)) {
+    if (Z_in && !is_device_ptr(Z_in)) {
         double *t = (double *)buf.get(nn * 8);
         if (!t) return SP2_ERR_NOMEM;
         CKS(cudaMemcpyAsync(t, Z_in, nn * 8, cudaMemcpyHostToDevice, s));
@@ -290,7 +282,7 @@ sp2_status run_fp64(const double *H_in, const double *Z_in, int N, double n_occ,
     k_energy64<<<rb, T64, 0, s>>>(Dfin, H, N, part);
     k_sum_parts<<<1, 32, 0, s>>>(part, rb, d_rec + 4 * (refine_layers + 1));
     CKS(cudaGetLastError());
-    if (is_dev(D_out)) CKS(cudaMemcpyAsync(D_out, Dfin, nn * 8, cudaMemcpyDeviceToDevice, s));
+    if (is_device_ptr(D_out)) CKS(cudaMemcpyAsync(D_out, Dfin, nn * 8, cudaMemcpyDeviceToDevice, s));
     else CKS(cudaMemcpyAsync(D_out, Dfin, nn * 8, cudaMemcpyDeviceToHost, s));
     std::vector<double> rec(4 * (refine_layers + 2));
     CKS(cudaMemcpyAsync(rec.data(), d_rec, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, s));

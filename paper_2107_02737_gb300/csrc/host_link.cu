@@ -56,6 +56,16 @@ __global__ void __launch_bounds__(LINK_THREADS) k_stage_lower(const double *__re
 
 }  // namespace
 
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 const void *mapped_host_ptr(const void *p) {
     if (!p) return nullptr;
     cudaPointerAttributes a;

@@ -7,6 +7,11 @@
 
 namespace sp2i {
 
+// True when the kernels of this device can use p directly: device memory or
+// managed memory.  Host memory (pageable or page-locked) and unknown pointers
+// give false.
+bool is_device_ptr(const void *p);
+
 // Device address through which the SMs can read and write the page-locked host
 // memory at p (mapped into this device's address space), or nullptr when p is
 // pageable, device memory, or not mapped.
