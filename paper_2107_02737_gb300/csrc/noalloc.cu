@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include "host_link.h"
 #include "sp2.h"
 
 namespace {
@@ -27,21 +28,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
 
-bool on_device(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 extern "C" sp2_status sp2_density_noalloc(const double *H, int N, double n_occ, double tol, float *D,
                                           sp2_stats *st, const sp2_opts *o, void *stream) {
     if (N < 1 || N > SP2_NOALLOC_MAX_N) return SP2_ERR_ARG;
-    if (!H || !D || !on_device(H) || !on_device(D)) return SP2_ERR_ARG;  // staging host data would allocate
+    if (!H || !D || !sp2i::is_device_ptr(H) || !sp2i::is_device_ptr(D)) return SP2_ERR_ARG;  // staging host data would allocate
     if (o && o->profile) return SP2_ERR_ARG;                              // timing events are not allowed here
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SP2_ERR_CUDA;
