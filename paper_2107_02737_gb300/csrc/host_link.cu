@@ -1,5 +1,5 @@
-// host_link.cu -- staging a host-resident symmetric FP64 matrix from its lower
-// triangle.
+// host_link.cu -- residency of the caller's pointers, and staging a host-resident
+// symmetric FP64 matrix from its lower triangle.
 //
 // A call with host-resident H is bound by the host link: this GB300's link moves
 // ~210 GB/s host -> device, with the copy engines or with SM loads alike, so the

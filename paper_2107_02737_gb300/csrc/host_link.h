@@ -1,5 +1,6 @@
-// host_link.h -- moving the symmetric inputs of a host-resident call across the
-// host link.  H is the Kohn-Sham matrix in a real basis, hence symmetric
+// host_link.h -- where a caller's matrices live (device, page-locked or pageable
+// host memory), and moving the symmetric inputs of a host-resident call across
+// the host link.  H is the Kohn-Sham matrix in a real basis, hence symmetric
 // (Section "The density matrix"), and the output kernel already reads only the
 // lower triangles of X_L and H; what crosses the link can therefore be halved.
 #pragma once
