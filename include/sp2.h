@@ -19,8 +19,10 @@
  *    pinned); the library detects which and stages host data through device
  *    memory.  Pinned (page-locked, mapped) host memory is accessed in place
  *    across the host link: of H (and of a response's H1) only the lower
- *    triangle, diagonal included, is read, and D (D1, dH) is written there
- *    directly by the output kernel.  Pageable host matrices are copied whole.
+ *    triangle, diagonal included, is read, and the FP32 results D (D1, dH)
+ *    are written there directly by the output kernel (the FP64 results of
+ *    sp2_density_refined / sp2_density_nonorth are copied back).  Pageable host
+ *    matrices, and the non-symmetric inputs G and Z, are copied whole.
  *    The caller owns every buffer it passes; the library frees none.
  *  - H must be symmetric (bit-exactly, as produced by (A + A^T)/2); the result
  *    for an asymmetric H is unspecified but finite (with pinned H it is that

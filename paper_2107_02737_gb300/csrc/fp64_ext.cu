@@ -204,12 +204,14 @@ sp2_status run_fp64(const double *H_in, const double *Z_in, int N, double n_occ,
     if (dev < 0 || dev >= 64) return SP2_ERR_CUDA;
     const size_t nn = (size_t)N * N;
     DevBuf buf(s);
-    // Inputs on the device.
+    // Inputs on the device: page-locked H from its lower triangle (as every entry
+    // point reads it), pageable H and any Z (not symmetric) copied whole.
     const double *H = H_in;
     if (!is_device_ptr(H_in)) {
         double *t = (double *)buf.get(nn * 8);
         if (!t) return SP2_ERR_NOMEM;
-        CKS(cudaMemcpyAsync(t, H_in, nn * 8, cudaMemcpyHostToDevice, s));
+        if (const void *m = mapped_host_ptr(H_in)) CKS(launch_stage_lower((const double *)m, t, N, s));
+        else CKS(cudaMemcpyAsync(t, H_in, nn * 8, cudaMemcpyHostToDevice, s));
         H = t;
     }
     const double *Z = Z_in;

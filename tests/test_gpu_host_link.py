@@ -126,3 +126,23 @@ def test_pinned_output_needs_no_staging():
     assert call(Dp) == sp2.OK
     assert torch.equal(Dp, ref.cpu())
     assert call(_pageable(np.zeros((n, n)), torch.float32)) == sp2.ERR_NOMEM
+
+
+def test_fp64_entry_points_read_pinned_h_from_its_lower_triangle():
+    """sp2_density_refined and sp2_density_nonorth follow the same convention: a
+    page-locked H is read from its lower triangle, a non-symmetric Z is copied whole."""
+    from oracle import density as odens
+
+    n = 300
+    ham = inputs.gapped_random(n, 150, inputs.rng_for(10, n))
+    scrambled = ham.H + np.triu(1e-3 * np.random.default_rng(4).standard_normal((n, n)), 1)
+    ref, _ = sp2.density_refined(dev(ham.H), ham.n_occ, refine_layers=1)
+    D, _ = sp2.density_refined(_pinned(scrambled), ham.n_occ, refine_layers=1)
+    assert D.device.type == "cpu"
+    assert float((D - ref.cpu()).abs().max()) <= 1e-12
+    S = inputs.overlap_matrix(n, inputs.rng_for(10, n + 1))
+    Z = odens.inverse_factor_cholesky(S)
+    assert not np.array_equal(Z, Z.T)
+    ref, _ = sp2.density_nonorth(dev(ham.H), dev(Z), ham.n_occ)
+    D, _ = sp2.density_nonorth(_pinned(scrambled), _pinned(Z), ham.n_occ)
+    assert float((D - ref.cpu()).abs().max()) <= 1e-12
