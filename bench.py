@@ -178,6 +178,28 @@ def l2_note(n):
     return f"{big} (H is {h_mb:.0f} MB FP64; split operands {op_mb:.0f} MB per layer; L2 129 MB)"
 
 
+# The stated agreement targets: ||D - D_fp64||_F / sqrt(N) <= 1e-3 for the split
+# 16-bit precisions and 1e-5 for FP32, |Tr D - n_occ| <= 1e-6.
+TOL_FRO = {"fp16": 1e-3, "bf16": 1e-3, "fp32": 1e-5}
+TOL_TRACE = 1e-6
+
+
+def tolerance_verdicts(line, n_occ, precision):
+    """Pass / fail of every stated tolerance for the numbers on this line (None = not measured)."""
+    def verdict(value, bound):
+        return {"value": value, "bound": bound, "ok": None if value is None else bool(abs(value) <= bound)}
+
+    acc, f32 = line["accuracy"], line["fp32_simt"]
+    out = {"split_fro_err": verdict(acc["fro_err_vs_fp64_per_sqrtN"], TOL_FRO[precision]),
+           "split_trace_err": verdict(acc["trace_err"], TOL_TRACE),
+           "fp32_fro_err": verdict(f32.get("fro_err_vs_fp64_per_sqrtN"), TOL_FRO["fp32"]),
+           "fp32_trace_err": verdict(f32["trace_err"], TOL_TRACE)}
+    if "refined" in line:
+        out["refined_trace_err"] = verdict(line["refined"]["trace_err"], TOL_TRACE)
+        out["refined_fro_err"] = verdict(line["refined"].get("fro_err_vs_fp64_per_sqrtN"), TOL_FRO[precision])
+    return out
+
+
 def eff_tflops(layers, n, ms):
     return layers * 2.0 * float(n) ** 3 / (ms * 1e-3) / 1e12
 
@@ -230,12 +252,18 @@ def cpu_baseline_leg(ham, gpu_choices, budget_s):
     per_layer = (time.perf_counter() - t0) / max(done, 1)
     L = len(gpu_choices)
     ms_to_d = per_layer * L * 1e3
+    # The oracle's definition of D: dense FP64 eigendecomposition (LAPACK dsyevd through
+    # numpy) and the outer product over the occupied eigenvectors, once, whole.
     t1 = time.perf_counter()
+    D_eigh = odens.density_matrix(ham.H, ham.n_occ)
+    t_eigh = time.perf_counter() - t1
+    del D_eigh
     D_ref = odens.density_from_eigensystem(ham.eigvecs, ham.n_occ)
-    t_ref = time.perf_counter() - t1
     return ({"value": eff_tflops(L, n, ms_to_d), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-             "sample": f"{done} of {L} FP64 SP2 layers at N={n} (DGEMM), extrapolated to {L} layers",
-             "ms_to_D": ms_to_d, "outer_product_s": t_ref}, D_ref)
+             "sample": (f"{done} of {L} FP64 SP2 layers at N={n} (DGEMM), extrapolated to {L} layers; "
+                        f"plus one whole eigendecomposition route (eigh + outer product) at N={n}"),
+             "ms_to_D": ms_to_d, "eigh_ms_to_D": 1e3 * t_eigh,
+             "gpu_speedup_vs_eigh": None}, D_ref)
 
 
 def main():
@@ -335,6 +363,8 @@ def main():
     peak_burst, peak_sus, peak_kind = peaks()
     k_ms = statistics.mean(kern_ms)
     achieved = eff_tflops(L, n, k_ms)
+    # The layer kernel runs ~25 ms at a time, back to back with short gaps: a burst,
+    # so the burst peak is the denominator; the sustained figure is kept beside it.
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -347,11 +377,12 @@ def main():
                      "commutator_fro": comm, "band_energy": res.band_energy},
         "fp32_simt": {"ms_per_step": ms32, "value": eff_tflops(r32.layers, n, ms32), "unit": "TFLOP/s",
                       "layers": r32.layers, "trace_err": r32.trace_D - n_occ, "speedup_split_vs_fp32": ms32 / ms},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
-                     "frac": achieved / peak_sus, "traffic": profiled_traffic(n, L, args.precision),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_burst, "unit": "TFLOP/s",
+                     "frac": achieved / peak_burst, "traffic": profiled_traffic(n, L, args.precision),
                      "kernel": "k_tc_persistent (all layers, one launch)", "kernel_ms": k_ms,
                      "algorithmic": f"{L} layers x 2N^3 flops",
-                     "peak_kind": f"{peak_kind} cuBLAS bf16 sustained (burst {peak_burst})"},
+                     "peak_kind": f"{peak_kind} cuBLAS bf16 burst",
+                     "peak_sustained": peak_sus, "frac_of_sustained": achieved / peak_sus},
         "aux_ms_per_step": statistics.mean(phase0),
         "e2e": {"value": world * eff_tflops(re2e.layers, n, e2e_ms), "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": n * (n + 1) // 2 * 8, "d2h_bytes_per_step": n * n * 4,
@@ -362,10 +393,12 @@ def main():
     }
     if not args.no_cpu_baseline:
         cpu, D_ref = cpu_baseline_leg(ham, res.choices, args.cpu_budget_s)
+        cpu["gpu_speedup_vs_eigh"] = cpu["eigh_ms_to_D"] / ms
         line["cpu_baseline"] = cpu
         line["accuracy"]["fro_err_vs_fp64_per_sqrtN"] = float(np.linalg.norm(D_host - D_ref) / np.sqrt(n))
         D32_host = D32.cpu().double().numpy()
         line["fp32_simt"]["fro_err_vs_fp64_per_sqrtN"] = float(np.linalg.norm(D32_host - D_ref) / np.sqrt(n))
+    line["tolerances"] = tolerance_verdicts(line, n_occ, args.precision)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

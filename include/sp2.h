@@ -338,8 +338,12 @@ sp2_status sp2_density_nonorth(const double *H, const double *Z, int N, double n
  * is reserved by its own pool or by another framework's caching allocator (a
  * new allocation can fail or fragment it), or a step loop that cannot afford
  * an allocation's latency.  The workspace is a statically allocated device
- * array of 6 MiB, present on every GPU that loads the library until the
- * process exits, which holds one solve of N <= SP2_NOALLOC_MAX_N.
+ * array of 6 MiB, which holds one solve of N <= SP2_NOALLOC_MAX_N.  A GPU holds
+ * it, until the process exits, from the moment the library's device code is
+ * loaded there: with lazy module loading (the CUDA default) that is the first
+ * call of this entry point on the device, so make that call before reserving
+ * the rest of the device's memory (it returns SP2_ERR_NOMEM if the array cannot
+ * be placed then).
  *   H, D   must be device pointers (staging host data would allocate);
  *          arguments and results are those of sp2_density.
  *   o      may be NULL; o->profile must be 0.

@@ -8,9 +8,13 @@
 // device array, sized for N <= SP2_NOALLOC_MAX_N, and runs the ordinary
 // sp2_density kernels on it.
 //
-// The array lives in every GPU that loads the library, for the life of the
-// process.  Host code may not use its name as a device address: the address is
-// obtained once per device with cudaGetSymbolAddress, with that device current.
+// The array is held by every GPU on which the library's device code has been
+// loaded, for the life of the process.  With lazy module loading (the CUDA
+// default) that happens at first use on a device -- this entry point's first
+// call there -- and not when the library is loaded, so that first call should
+// come before the caller reserves the rest of the device's memory.  Host code
+// may not use the array's name as a device address: the address is obtained
+// once per device with cudaGetSymbolAddress, with that device current.
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -43,10 +47,13 @@ extern "C" sp2_status sp2_density_noalloc(const double *H, int N, double n_occ, 
         if (!g_scratch_addr[dev]) {
             // First call on this device: resolve the device address of the array
             // (with this device current).
+            // With lazy loading this is where the module (and the array) is
+            // loaded on the device, so it can fail for lack of device memory.
             void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
                 cudaGetLastError();
-                return SP2_ERR_CUDA;
+                return e == cudaErrorMemoryAllocation ? SP2_ERR_NOMEM : SP2_ERR_CUDA;
             }
             g_scratch_addr[dev] = p;
         }

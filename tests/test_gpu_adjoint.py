@@ -46,6 +46,7 @@ def test_adjoint_directional_differences(case):
     h = 1e-4
     f = lambda s: np.sum(odens.density_matrix(ham.H + s * E, ham.n_occ) * G)
     fd = (f(h) - f(-h)) / (2 * h)
+    print(f"\nadjoint vs central difference: rel err {abs(np.sum(E * host(dH)) - fd) / abs(fd):.2e}")
     assert np.sum(E * host(dH)) == pytest.approx(fd, rel=3e-3)
 
 
@@ -56,6 +57,7 @@ def test_adjoint_response_duality_on_gpu(case):
     _, D1, _ = sp2.response(dev(ham.H), dev(E), ham.n_occ, precision="fp16", fwd=res)
     lhs = np.sum(E * host(dH))
     rhs = np.sum(G * host(D1))
+    print(f"\nduality: rel gap {abs(lhs - rhs) / abs(rhs):.2e}")
     assert lhs == pytest.approx(rhs, rel=2e-3)
 
 
@@ -146,4 +148,4 @@ def test_adjoint_differentiation_workload_4096_checkpointed():
     got = host(g1[torch.tensor(pick, device="cuda")])
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     print(f"\nN=4096 adjoint (checkpointed): layers={r1.layers} sampled-row rel err {err:.2e}")
-    assert err <= 1e-2
+    assert err <= 2e-4  # measured 1.4e-5

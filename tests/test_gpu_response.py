@@ -14,8 +14,9 @@ from tests._gpu import TOL_D, dev, fro_err, host, rel_err
 pytestmark = pytest.mark.gpu
 
 # ||D1 - D1_ref||_F / ||D1_ref||_F for the split precisions (FP32 accumulation of a
-# chain whose derivative amplifies near-gap components by up to 1/gap).
-TOL_D1 = {"fp16": 2e-3, "bf16": 2e-2}
+# chain whose derivative amplifies near-gap components by up to 1/gap): about ten
+# times the errors measured on these cases (FP16 8e-6 against the chain).
+TOL_D1 = {"fp16": 1e-4, "bf16": 2e-2}
 
 
 @pytest.fixture(scope="module", params=[256, 300])
@@ -37,7 +38,7 @@ def test_response_matches_chain_and_theta(case, precision):
     g = host(D1)
     print(f"\n{precision} N={ham.n}: rel err vs chain {rel_err(g, chain):.2e}, vs theta {rel_err(g, theta):.2e}")
     assert rel_err(g, chain) <= TOL_D1[precision]
-    assert rel_err(g, theta) <= TOL_D1[precision] + 1e-3
+    assert rel_err(g, theta) <= 2 * TOL_D1[precision]
     assert np.array_equal(g, g.T)
     assert abs(np.trace(g)) <= 1e-3 * np.linalg.norm(g)
 
@@ -47,7 +48,8 @@ def test_response_matches_oracle_central_differences(case):
     h = 1e-4
     fd = (odens.density_matrix(ham.H + h * H1, ham.n_occ) - odens.density_matrix(ham.H - h * H1, ham.n_occ)) / (2 * h)
     _, D1, _ = sp2.response(dev(ham.H), dev(H1), ham.n_occ, precision="fp16")
-    assert rel_err(host(D1), fd) <= TOL_D1["fp16"] + 1e-3
+    print(f"\nN={ham.n} response vs central differences: rel err {rel_err(host(D1), fd):.2e}")
+    assert rel_err(host(D1), fd) <= 2 * TOL_D1["fp16"]
 
 
 def test_response_replaying_forward_matches_density(case):
@@ -78,4 +80,4 @@ def test_response_differentiation_workload_4096():
     got = host(D1[torch.tensor(pick, device="cuda")])
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     print(f"\nN=4096 response: layers={res.layers} sampled-row rel err {err:.2e}")
-    assert err <= 1e-2
+    assert err <= 1e-4  # measured 6.6e-6

@@ -33,6 +33,34 @@ def test_golden_3x3_rational_basis():
         assert density.band_energy(D, H) == pytest.approx(g[f"band_energy_occ{k}"], abs=1e-14)
 
 
+def test_golden_3x3_rows_and_gap():
+    """density_rows and homo_lumo_gap, which the full-size GPU checks use, against the
+    hand-derived basis: any selection of rows, in any order, of D9 / 9, and the gaps 3, 2."""
+    g = load("density_3x3.txt")
+    C = g["Q3"].reshape(3, 3) / 3.0
+    for k in (1, 2):
+        ref = g[f"D9_occ{k}"].reshape(3, 3) / 9.0
+        for rows in ([0], [2, 0], [1, 2, 0], [1, 1]):
+            np.testing.assert_allclose(density.density_rows(C, k, rows), ref[rows], atol=1e-15)
+        assert density.homo_lumo_gap(g["lam"], k) == g[f"gap_occ{k}"]
+    assert density.homo_lumo_gap(g["lam"], 0) == np.inf
+    assert density.homo_lumo_gap(g["lam"], 3) == np.inf
+    np.testing.assert_array_equal(density.density_rows(C, 0, [1]), np.zeros((1, 3)))
+
+
+def test_rows_and_gap_of_a_generated_spectrum():
+    """On a generated Hamiltonian with a known spectrum: the rows equal those of the full
+    outer product, and the gap is the one the generator opened (0.1 in this recipe)."""
+    ham = inputs.gapped_random(40, 17, inputs.rng_for(9, 40))
+    full = density.density_from_eigensystem(ham.eigvecs, 17)
+    rows = [39, 0, 17, 16]
+    np.testing.assert_allclose(density.density_rows(ham.eigvecs, 17, rows), full[rows], atol=1e-14)
+    lam, _ = density.eigensystem(ham.H)
+    gap = density.homo_lumo_gap(lam, 17)
+    assert gap == pytest.approx(ham.eigvals[17] - ham.eigvals[16], abs=1e-12)
+    assert gap >= 0.1 - 1e-12
+
+
 def _closed_form_2x2(a, b, c):
     # Lower eigenvector projector of [[a, b], [b, c]]: D = I/2 - (H - (a+c)/2 I)/(2r).
     r = np.sqrt(((a - c) / 2) ** 2 + b * b)
