@@ -33,10 +33,10 @@ def test_adjoint_matches_chain_and_theta(case, precision):
     g = host(dH)
     chain = osp2.chain_adjoint(ham.H, G, res.choices, res.eps_min, res.eps_max)
     theta = odens.adjoint(ham.H, G, ham.n_occ)
-    tol = 2e-3 if precision == "fp16" else 2e-2
+    tol = 1e-4 if precision == "fp16" else 3e-4   # about ten times the measured 1.1e-5 / 2.8e-5
     print(f"\n{precision}: rel err vs chain {rel_err(g, chain):.2e}, vs theta {rel_err(g, theta):.2e}")
     assert rel_err(g, chain) <= tol
-    assert rel_err(g, theta) <= tol + 1e-3
+    assert rel_err(g, theta) <= 2 * tol
     assert np.array_equal(g, g.T)
 
 
@@ -47,7 +47,7 @@ def test_adjoint_directional_differences(case):
     f = lambda s: np.sum(odens.density_matrix(ham.H + s * E, ham.n_occ) * G)
     fd = (f(h) - f(-h)) / (2 * h)
     print(f"\nadjoint vs central difference: rel err {abs(np.sum(E * host(dH)) - fd) / abs(fd):.2e}")
-    assert np.sum(E * host(dH)) == pytest.approx(fd, rel=3e-3)
+    assert np.sum(E * host(dH)) == pytest.approx(fd, rel=1e-4)   # measured 9.5e-6
 
 
 def test_adjoint_response_duality_on_gpu(case):
@@ -58,7 +58,7 @@ def test_adjoint_response_duality_on_gpu(case):
     lhs = np.sum(E * host(dH))
     rhs = np.sum(G * host(D1))
     print(f"\nduality: rel gap {abs(lhs - rhs) / abs(rhs):.2e}")
-    assert lhs == pytest.approx(rhs, rel=2e-3)
+    assert lhs == pytest.approx(rhs, rel=3e-5)   # measured 2.2e-6
 
 
 def test_autograd_function(case):
@@ -148,4 +148,4 @@ def test_adjoint_differentiation_workload_4096_checkpointed():
     got = host(g1[torch.tensor(pick, device="cuda")])
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     print(f"\nN=4096 adjoint (checkpointed): layers={r1.layers} sampled-row rel err {err:.2e}")
-    assert err <= 2e-4  # measured 1.4e-5
+    assert err <= 3e-4  # measured 3.1e-5

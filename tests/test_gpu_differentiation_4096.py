@@ -35,7 +35,7 @@ def test_response_central_differences_4096(workload):
     got = float(np.sum(0.5 * (G + G.T) * host(D1)))
     err = abs(got - fd) / abs(fd)
     print(f"\nN=4096 response: Tr[G D1] = {got:.10e}, central difference {fd:.10e}, rel err {err:.2e}")
-    assert err <= 1e-3
+    assert err <= 1e-4   # measured 1.0e-5
 
 
 def test_adjoint_central_differences_4096(workload):
@@ -45,4 +45,4 @@ def test_adjoint_central_differences_4096(workload):
     got = float(np.sum(H1 * host(dH)))
     err = abs(got - fd) / abs(fd)
     print(f"\nN=4096 adjoint: <H1, dH> = {got:.10e}, central difference {fd:.10e}, rel err {err:.2e}")
-    assert err <= 1e-3
+    assert err <= 1e-4   # measured 1.3e-5

@@ -15,8 +15,8 @@ pytestmark = pytest.mark.gpu
 
 # ||D1 - D1_ref||_F / ||D1_ref||_F for the split precisions (FP32 accumulation of a
 # chain whose derivative amplifies near-gap components by up to 1/gap): about ten
-# times the errors measured on these cases (FP16 8e-6 against the chain).
-TOL_D1 = {"fp16": 1e-4, "bf16": 2e-2}
+# times the errors measured on these cases (FP16 4e-6, BF16 1.7e-5 against the chain).
+TOL_D1 = {"fp16": 1e-4, "bf16": 2e-4}
 
 
 @pytest.fixture(scope="module", params=[256, 300])
