@@ -166,6 +166,12 @@ typedef struct {
                              up to (s - 1)/s of the forward's squares again.  -1 = the s that needs
                              the least memory for the chain's length.  A stride that would not
                              save memory keeps every layer.  Range -1 .. SP2_MAX_LAYERS_LIMIT. */
+    int exact_slices;     /* sp2_density_refined, sp2_density_nonorth and sp2_congruence only: integer
+                             slices per operand row in their exact-slice products, 4, 5 or 6 (0 = 6).
+                             A row keeps 11 + b (S - 1) bits relative to its 2-norm (b = 6 bits per
+                             further slice up to N = 8192, fewer above); the products take 10, 15 or
+                             21 slice products per tile: fewer slices are faster and less accurate
+                             (S = 4: about 2^-29 of the row norms, 5: 2^-35, 6: 2^-41). */
 } sp2_opts;
 
 /* Fill `o` with the defaults. */
@@ -307,14 +313,25 @@ sp2_status sp2_apply_layers(const float *X0, int N, const int *choices, int n_la
  * further layers with X held in FP64 (section "Deep-neural network electronic
  * structure solver": extra layers with a double-precision representation of X
  * act as a refinement that purifies the eigenvalues closer to 1 and 0).  Each
- * refinement layer takes its sign by the same trace rule, decided on the device;
- * the square is an FP64 GEMM emulated on the tensor cores (cuBLAS).
+ * refinement layer takes its sign by the same trace rule, decided on the device.
+ * The refinement squares are exact-slice products on the FP16 tensor cores:
+ * Y = X - I/2 is carried in 64-bit fixed point (units of 2^-54 up to N = 8192)
+ * and split into six small-integer slices (an 11-bit leading slice, then 6 bits
+ * each: about 2^-41 of the row norms); the slice products are integer matrices
+ * summed exactly in the FP32 accumulators and combined in 64-bit integer
+ * arithmetic, so a layer's square is accurate to about 1e-13 per element.
  *   refine_layers [in]  0 .. 8 (the paper uses two).
  *   D             [out] N x N FP64, the refined density matrix.
  *   st            [out] the chain's layers followed by the refinement layers;
- *                       trace_D and band_energy from the FP64 result.
- * Allocates device memory for the FP64 matrices (3 N^2 doubles + the chain's
- * workspace) and frees it before returning.
+ *                       trace_D and band_energy from the FP64 result; with
+ *                       o->profile, phase_ms holds the device time of [0] the
+ *                       chain (and sp2_density_nonorth's first congruence), [1] the
+ *                       refinement layers, [2] the back-transformation and the FP64
+ *                       Tr[D H], [3] all of it (CUDA events on the call's stream).
+ * Allocates device memory for the FP64 and fixed-point matrices (about 50 bytes
+ * per element plus the chain's workspace) and frees it before returning.
+ * Returns SP2_ERR_NOT_CONVERGED also when X leaves [-2^-13, 1 + 2^-13]
+ * spectrally during the refinement (its slices could not hold it exactly).
  */
 sp2_status sp2_density_refined(const double *H, int N, double n_occ, double tol, int refine_layers, double *D,
                                sp2_stats *st, const sp2_opts *o, void *stream);
@@ -323,13 +340,30 @@ sp2_status sp2_density_refined(const double *H, int N, double n_occ, double tol,
  * sp2_density_nonorth -- density matrix in a non-orthogonal basis (section "The
  * density matrix"): with Z an inverse factor of the overlap S (Z^T S Z = I),
  * H_orth = Z^T H Z, D_orth = theta(mu I - H_orth) by the chain (plus
- * `refine_layers` FP64 layers), and D = Z D_orth Z^T.  The congruences are FP64
- * GEMMs emulated on the tensor cores.  D does not depend on which Z is given.
+ * `refine_layers` FP64 layers), and D = Z D_orth Z^T.  The congruences are
+ * sp2_congruence's products.  D does not depend on which Z is given.
  *   Z [in]  N x N FP64, row-major.
  *   D [out] N x N FP64; band_energy = Tr[D H].
  */
 sp2_status sp2_density_nonorth(const double *H, const double *Z, int N, double n_occ, double tol,
                                int refine_layers, double *D, sp2_stats *st, const sp2_opts *o, void *stream);
+
+/*
+ * sp2_congruence -- the orthogonalisation step of section "The density matrix":
+ *   side = 0: out = Z^T M Z  (H_orth from H in a non-orthogonal basis),
+ *   side = 1: out = Z M Z^T  (D from D_orth).
+ * Z, M, out: N x N FP64, row-major, device memory; M symmetric; out is exactly
+ * symmetric (its lower triangle mirrors the upper).  Both products are
+ * exact-slice products on the FP16 tensor cores: every row of an operand is
+ * scaled by a power of two at or above its 2-norm and split into six
+ * small-integer slices whose products are summed exactly in the FP32
+ * accumulators, so each entry of a product is accurate to about 2^-41 of the
+ * product of its row's and column's 2-norms.  Allocates about 60 bytes per
+ * element of device memory for the call.  Returns SP2_ERR_ARG for host pointers
+ * or side not in {0, 1}.
+ */
+sp2_status sp2_congruence(const double *Z, const double *M, int N, int side, double *out, const sp2_opts *o,
+                          void *stream);
 
 /*
  * sp2_density_noalloc -- sp2_density without any device allocation.

@@ -4,8 +4,8 @@
 
 Each CUDA translation unit under csrc/ is compiled to an object in parallel and
 the objects are linked into ``paper_2107_02737_gb300/libsp2.so`` (CUDA runtime
-linked statically, so the library loads without a GPU driver present; cuBLAS,
-used for the FP64 GEMMs around the chain, linked dynamically).
+linked statically, so the library loads without a GPU driver present; no other
+library is linked: every matrix product runs in this library's own kernels).
 """
 from __future__ import annotations
 
@@ -22,8 +22,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsp2.so")
-SOURCES = ["aux_kernels.cu", "simt_kernel.cu", "tc_kernel.cu", "api.cu", "noalloc.cu", "fp64_ext.cu",
-           "host_link.cu"]
+SOURCES = ["aux_kernels.cu", "simt_kernel.cu", "tc_kernel.cu", "exact_kernel.cu", "api.cu", "noalloc.cu",
+           "fp64_ext.cu", "host_link.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 
@@ -61,7 +61,7 @@ def build(force: bool = False, jobs: int = 4, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, jobs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcublas"]
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

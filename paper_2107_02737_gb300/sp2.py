@@ -45,14 +45,15 @@ class Opts(ctypes.Structure):
                 ("user_bounds", ctypes.c_int), ("test_hook", ctypes.c_int), ("eps_min", ctypes.c_double),
                 ("eps_max", ctypes.c_double), ("profile", ctypes.c_int), ("cta_group", ctypes.c_int),
                 ("accelerate", ctypes.c_int), ("eps_homo", ctypes.c_double), ("eps_lumo", ctypes.c_double),
-                ("checkpoint_stride", ctypes.c_int)]
+                ("checkpoint_stride", ctypes.c_int), ("exact_slices", ctypes.c_int)]
 
 
 EXPORTS = ["sp2_default_opts", "sp2_status_string", "sp2_device_info", "sp2_density", "sp2_density_workspace_bytes",
            "sp2_response", "sp2_response_workspace_bytes", "sp2_adjoint", "sp2_adjoint_workspace_bytes",
            "sp2_density_batched", "sp2_density_batched_workspace_bytes", "sp2_apply_layers",
            "sp2_density_noalloc", "sp2_density_refined", "sp2_density_nonorth", "sp2_batch_plan_create",
-           "sp2_batch_plan_launch", "sp2_batch_plan_stats", "sp2_batch_plan_cta_group", "sp2_batch_plan_destroy"]
+           "sp2_batch_plan_launch", "sp2_batch_plan_stats", "sp2_batch_plan_cta_group", "sp2_batch_plan_destroy",
+           "sp2_congruence"]
 NOALLOC_MAX_N = 512
 
 _lib = None
@@ -113,6 +114,8 @@ def load() -> ctypes.CDLL:
     lib.sp2_batch_plan_cta_group.restype = c_i
     lib.sp2_batch_plan_destroy.argtypes = [c_p]
     lib.sp2_batch_plan_destroy.restype = None
+    lib.sp2_congruence.argtypes = [c_p, c_p, c_i, c_i, c_p, P(Opts), c_p]
+    lib.sp2_congruence.restype = c_i
     _lib = lib
     return lib
 
@@ -456,14 +459,16 @@ def density_noalloc(H: torch.Tensor, n_occ: int, out: torch.Tensor, tol: float =
 
 def density_refined(H: torch.Tensor, n_occ: int, refine_layers: int = 2, tol: float = 1e-6,
                     precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0, stream=None,
-                    gap: Optional[Sequence[float]] = None):
+                    gap: Optional[Sequence[float]] = None, exact_slices: int = 0, profile: bool = False):
     """The chain plus ``refine_layers`` FP64 layers; returns (D float64, Result).  ``gap`` as for
-    ``density`` (the FP64 layers are plain)."""
+    ``density`` (the FP64 layers are plain); ``exact_slices`` (4..6, 0 = 6) sets the accuracy of
+    the refinement squares; ``profile`` fills Result.phase_ms with device times."""
     H = _f64(H, "H")
     n = _square(H, "H")
     D = torch.empty((n, n), dtype=torch.float64, device=H.device)
     st = _new_stats()
-    o = make_opts(precision, max_layers, timeout_ms, gap=gap)
+    o = make_opts(precision, max_layers, timeout_ms, gap=gap, profile=profile)
+    o.exact_slices = int(exact_slices)
     s = load().sp2_density_refined(ctypes.c_void_p(H.data_ptr()), n, float(n_occ), float(tol), int(refine_layers),
                                    ctypes.c_void_p(D.data_ptr()), ctypes.byref(st), ctypes.byref(o),
                                    ctypes.c_void_p(_stream_handle(H, stream)))
@@ -472,18 +477,37 @@ def density_refined(H: torch.Tensor, n_occ: int, refine_layers: int = 2, tol: fl
 
 
 def density_nonorth(H: torch.Tensor, Z: torch.Tensor, n_occ: int, refine_layers: int = 0, tol: float = 1e-6,
-                    precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0, stream=None):
+                    precision: str = "fp16", max_layers: int = 100, timeout_ms: float = 2000.0, stream=None,
+                    exact_slices: int = 0):
     """D = Z theta(mu I - Z^T H Z) Z^T (float64) for an inverse overlap factor Z; returns (D, Result)."""
     H, Z = _f64(H, "H"), _f64(Z, "Z")
     n = _square(H, "H")
     D = torch.empty((n, n), dtype=torch.float64, device=H.device)
     st = _new_stats()
     o = make_opts(precision, max_layers, timeout_ms)
+    o.exact_slices = int(exact_slices)
     s = load().sp2_density_nonorth(ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(Z.data_ptr()), n, float(n_occ),
                                    float(tol), int(refine_layers), ctypes.c_void_p(D.data_ptr()), ctypes.byref(st),
                                    ctypes.byref(o), ctypes.c_void_p(_stream_handle(H, stream)))
     _check(s, "sp2_density_nonorth")
     return D, _result(s, st)
+
+
+def congruence(Z: torch.Tensor, M: torch.Tensor, side: int = 0, timeout_ms: float = 2000.0, stream=None,
+               exact_slices: int = 0):
+    """Z^T M Z (side 0) or Z M Z^T (side 1) for symmetric M, float64 device tensors; returns the result."""
+    Z, M = _f64(Z, "Z"), _f64(M, "M")
+    n = _square(Z, "Z")
+    if _square(M, "M") != n:
+        raise ValueError("Z and M must have the same size")
+    out = torch.empty((n, n), dtype=torch.float64, device=M.device)
+    o = make_opts("fp16", timeout_ms=timeout_ms)
+    o.exact_slices = int(exact_slices)
+    s = load().sp2_congruence(ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(M.data_ptr()), n, int(side),
+                              ctypes.c_void_p(out.data_ptr()), ctypes.byref(o),
+                              ctypes.c_void_p(_stream_handle(M, stream)))
+    _check(s, "sp2_congruence")
+    return out
 
 
 def device_info():
