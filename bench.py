@@ -200,6 +200,35 @@ def tolerance_verdicts(line, n_occ, precision):
     return out
 
 
+def exact_product_flops(n, slices=6):
+    """Tensor-core flops one refinement square executes: every 256 x 128 tile of the upper
+    triangle, one FP16 product (2 x 256 x 128 x K) per pair of slices with s + t < S."""
+    np_ = -(-n // 128) * 128
+    nbj, nbi = np_ // 128, -(-np_ // 256)
+    tiles = sum(max(0, nbj - 2 * b) for b in range(nbi))
+    return tiles * (slices * (slices + 1) // 2) * 2.0 * 256 * 128 * np_
+
+
+def refined_record(runs, n, n_occ, idem):
+    """The refined path's timing and accuracy (two FP64 layers after the split chain)."""
+    peak_burst, _, peak_kind = peaks()
+    ms = statistics.mean(r.phase_ms[3] for r in runs)
+    ms_ref = statistics.mean(r.phase_ms[1] for r in runs)
+    r = runs[-1]
+    chain_layers = r.layers - 2
+    executed = 2 * exact_product_flops(n) / (ms_ref * 1e-3) / 1e12
+    return {"ms_to_D": ms, "chain_ms": statistics.mean(q.phase_ms[0] for q in runs), "refine_ms": ms_ref,
+            "refine_layers": 2, "layers": r.layers, "trace_err": r.trace_D - n_occ, "idempotency_fro": idem,
+            "value": (chain_layers + 2) * 2.0 * float(n) ** 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "fro_err_vs_fp64_per_sqrtN": None,
+            "roofline": {"bound": "tensor", "achieved": executed, "peak": peak_burst, "unit": "TFLOP/s",
+                         "frac": executed / peak_burst, "traffic": None,
+                         "kernel": "k_exact_product<6> (two launches) with the slicing, decision and output "
+                                   "kernels of the refinement phase",
+                         "algorithmic": "executed FP16 tensor flops: 21 slice products per 256x128 upper tile",
+                         "peak_kind": f"{peak_kind} cuBLAS bf16 burst"}}
+
+
 def eff_tflops(layers, n, ms):
     return layers * 2.0 * float(n) ** 3 / (ms * 1e-3) / 1e12
 
@@ -341,6 +370,20 @@ def main():
     torch.cuda.synchronize()
     ms32 = e0.elapsed_time(e1) / args.fp32_steps
 
+    # ---- FP64 refinement: two further layers with X in double precision ----
+    # Device time from H to the refined FP64 D (CUDA events on the call's stream: chain,
+    # refinement layers, FP64 output); the call allocates its own buffers, outside that time.
+    ref_runs = []
+    for k in range(4):
+        D64, rref = sp2.density_refined(H, n_occ, refine_layers=2, precision=args.precision, profile=True)
+        if k > 0:
+            ref_runs.append(rref)
+    torch.cuda.synchronize()
+    ref_idem = float(torch.linalg.norm(D64 @ D64 - D64))
+    refined = refined_record(ref_runs, n, n_occ, ref_idem)
+    D64_host = D64.cpu().numpy()
+    del D64
+
     # ---- end to end through the API with pinned host buffers ----
     # The library reads page-locked H in place across the host link, its lower
     # triangle only (H is symmetric), and writes D in place: h2d n(n+1)/2 FP64
@@ -388,6 +431,7 @@ def main():
                 "h2d_bytes_per_step": n * (n + 1) // 2 * 8, "d2h_bytes_per_step": n * n * 4,
                 "host_buffers": "page-locked; H read in place (lower triangle), D written in place",
                 "equal_to_device_result": e2e_same},
+        "refined": refined,
         "clocks": clk.summary(),
         "gpu_launches": launches_per_step * args.steps,
     }
@@ -398,6 +442,7 @@ def main():
         line["accuracy"]["fro_err_vs_fp64_per_sqrtN"] = float(np.linalg.norm(D_host - D_ref) / np.sqrt(n))
         D32_host = D32.cpu().double().numpy()
         line["fp32_simt"]["fro_err_vs_fp64_per_sqrtN"] = float(np.linalg.norm(D32_host - D_ref) / np.sqrt(n))
+        line["refined"]["fro_err_vs_fp64_per_sqrtN"] = float(np.linalg.norm(D64_host - D_ref) / np.sqrt(n))
     line["tolerances"] = tolerance_verdicts(line, n_occ, args.precision)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -10,8 +10,11 @@
   every layer kept and with checkpointed recomputation; counts 2 N^3 (forward) +
   2 N^3 (reverse) per layer.
 * ``md``       — H_k = H_0 + sin(0.05 k) V through sp2_response (see md.py).
-* ``refined``  — the N = 8192 chain plus two FP64 refinement layers (cuBLAS FP64
-  emulated on the tensor cores); reports the added time and the trace.
+* ``refined``  — the N = 8192 chain plus two FP64 refinement layers (exact-slice
+  products on the FP16 tensor cores) for 4, 5 and 6 slices; device time of the chain,
+  the refinement and the whole call (profile events), trace and idempotency.
+* ``nonorth``  — the congruences Z^T H Z and Z D Z^T at N = 4096 (sp2_congruence),
+  and the whole non-orthogonal route; effective TFLOP/s count 4 N^3 per congruence.
 * ``accel``    — the N = 8192 chain, plain and accelerated from the generator's exact
   HOMO / LUMO (and from an interval four gaps wide around it); ms to D and layers.
 * ``host``     — the N = 8192 chain called with host-resident H and D: page-locked
@@ -107,14 +110,48 @@ def adjoint(steps, warmup, n=4096):
     return out
 
 
-def refined(steps, warmup, n=8192, layers=2):
+def refined(steps, warmup, n=8192, layers=2, slice_counts=(4, 5, 6)):
     ham = inputs.water_like_workload(n)
     H = torch.tensor(ham.H, device="cuda")
-    ms_chain, (_, r0) = _time(lambda: sp2.density(H, ham.n_occ), steps, warmup)
-    ms, (D, res) = _time(lambda: sp2.density_refined(H, ham.n_occ, refine_layers=layers), steps, warmup)
-    return {"workload": f"refined N={n}", "refine_layers": layers, "ms_per_step": ms, "chain_ms": ms_chain,
-            "refinement_ms": ms - ms_chain, "trace_err": res.trace_D - ham.n_occ,
-            "chain_trace_err": r0.trace_D - ham.n_occ, "idem_fro": float(torch.linalg.norm(D @ D - D))}
+    ws = torch.empty(sp2.workspace_bytes(n, "density"), dtype=torch.uint8, device="cuda")
+    ms_chain, (_, r0) = _time(lambda: sp2.density(H, ham.n_occ, workspace=ws), steps, warmup)
+    out = {"workload": f"refined N={n}", "refine_layers": layers, "chain_ms": ms_chain,
+           "chain_trace_err": r0.trace_D - ham.n_occ}
+    for slices in slice_counts:
+        runs = []
+        for k in range(warmup + steps):
+            D, res = sp2.density_refined(H, ham.n_occ, refine_layers=layers, exact_slices=slices, profile=True)
+            if k >= warmup:
+                runs.append(res.phase_ms)
+        torch.cuda.synchronize()
+        mean = [float(np.mean([r[i] for r in runs])) for i in range(4)]
+        out[f"slices_{slices}"] = {"device_ms_to_D": mean[3], "chain_device_ms": mean[0],
+                                   "refinement_device_ms": mean[1], "output_device_ms": mean[2],
+                                   "trace_err": res.trace_D - ham.n_occ,
+                                   "idem_fro": float(torch.linalg.norm(D @ D - D))}
+    return out
+
+
+def nonorth(steps, warmup, n=4096):
+    rng = inputs.rng_for(6, n)
+    ham = inputs.water_like_workload(n)
+    S = inputs.overlap_matrix(n, rng)
+    lam, U = np.linalg.eigh(S)
+    Z = torch.tensor((U / np.sqrt(lam)) @ U.T, device="cuda")     # Lowdin factor S^(-1/2)
+    Sh = (U * np.sqrt(lam)) @ U.T
+    Hn = Sh @ ham.H @ Sh
+    H = torch.tensor(0.5 * (Hn + Hn.T), device="cuda")
+    out = {"workload": f"non-orthogonal route N={n}"}
+    for side in (0, 1):
+        ms, C = _time(lambda: sp2.congruence(Z, H, side), steps, warmup)
+        out[f"congruence_side{side}_ms"] = ms
+        out[f"congruence_side{side}_tflops"] = 4.0 * n ** 3 / (ms * 1e-3) / 1e12
+    ms, (D, res) = _time(lambda: sp2.density_nonorth(H, Z, ham.n_occ, refine_layers=2), steps, warmup)
+    Sd = torch.tensor(S, device="cuda")
+    out.update({"nonorth_ms": ms, "layers": res.layers,
+                "trace_DS_err": float(torch.trace(D @ Sd)) - ham.n_occ,
+                "DSD_minus_D_fro": float(torch.linalg.norm(D @ Sd @ D - D))})
+    return out
 
 
 def accel(steps, warmup, n=8192, precision="fp16"):
@@ -166,12 +203,14 @@ def host(steps, warmup, n=8192, precision="fp16"):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", choices=["batched", "response", "adjoint", "md", "refined", "accel", "host"],
-                    required=True)
+    ap.add_argument("--workload", choices=["batched", "response", "adjoint", "md", "refined", "nonorth", "accel",
+                                           "host"], required=True)
     ap.add_argument("--accelerate", action="store_true", help="md: reuse HOMO / LUMO estimates step to step")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--layers", type=int, default=2, help="refined: FP64 refinement layers")
+    ap.add_argument("--slices", type=int, default=0, help="refined: one slice count (4..6) instead of all three")
     a = ap.parse_args(argv)
     if a.workload == "batched":
         out = batched(a.steps, a.warmup)
@@ -180,7 +219,9 @@ def main(argv=None) -> int:
     elif a.workload == "adjoint":
         out = adjoint(a.steps, a.warmup, a.n or 4096)
     elif a.workload == "refined":
-        out = refined(a.steps, a.warmup, a.n or 8192)
+        out = refined(a.steps, a.warmup, a.n or 8192, a.layers, (a.slices,) if a.slices else (4, 5, 6))
+    elif a.workload == "nonorth":
+        out = nonorth(a.steps, a.warmup, a.n or 4096)
     elif a.workload == "accel":
         out = accel(a.steps, a.warmup, a.n or 8192)
     elif a.workload == "host":
