@@ -125,8 +125,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = ["paper_2107_02737_gb300/csrc/tc_kernel.cu", "paper_2107_02737_gb300/csrc/device_common.cuh",
-                  "paper_2107_02737_gb300/csrc/sp2_internal.h"]
+KERNEL_SOURCES = ["paper_2107_02737_gb300/csrc/tc_kernel.cu", "paper_2107_02737_gb300/csrc/tc_ptx.cuh",
+                  "paper_2107_02737_gb300/csrc/device_common.cuh", "paper_2107_02737_gb300/csrc/sp2_internal.h"]
 
 
 def kernel_source_sha():

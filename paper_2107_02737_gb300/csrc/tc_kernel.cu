@@ -71,8 +71,11 @@ struct TcSmemTail {
     uint64_t empty[MAX_STAGES];
     uint64_t tfull[2];
     uint64_t tempty[2];
+    uint64_t drain;                  // MMA completion, waited for when the launch aborts
     uint32_t tmem_base;
     uint32_t pad;
+    unsigned int issued;             // producer: ring stages this CTA has loaded into
+    unsigned int consumed;           // MMA thread (even CTA): stages whose copies it has waited for
     double red[EPI_WARPS][4];
     RoundCtl rc;
 };
@@ -103,6 +106,14 @@ struct TileWork {
     float cf;            // offset c of the input X: true X = stored X + c I
     float alpha;         // expansion a of the layer (1 = plain)
 };
+
+// Stop this CTA's roles, and for a CTA pair its peer's (so that neither waits for
+// signals the other will no longer send).
+template <int CG>
+__device__ __forceinline__ void tc_abort(RoundCtl &rc, uint32_t peer_abort) {
+    rc.abort = 1;
+    if (CG == 2) asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1) : "memory");
+}
 
 __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams &p, int g) {
     TileWork w;
@@ -170,6 +181,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             mbar_init(&tl.tfull[a], 1);
             mbar_init(&tl.tempty[a], EPI_WARPS * CG);  // one arrival per epilogue warp of the pair
         }
+        mbar_init(&tl.drain, 1);
+        tl.issued = 0;
+        tl.consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         round_ctl_init(rc, p);
@@ -195,11 +209,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     tc_fence_after();
     const uint32_t tmem_base = tl.tmem_base;
 
-    // Cluster addresses of the even CTA's barriers (the pair's MMA side).
-    uint32_t lead_full0 = 0, lead_tempty0 = 0;
+    // Cluster addresses of the even CTA's barriers (the pair's MMA side) and of the
+    // peer's abort flag.
+    uint32_t lead_full0 = 0, lead_tempty0 = 0, peer_abort = 0;
     if (CG == 2) {
         lead_full0 = cluster_addr(&tl.full[0], 0);
         lead_tempty0 = cluster_addr(&tl.tempty[0], 0);
+        peer_abort = cluster_addr(&rc.abort, rank ^ 1u);
     }
 
     // Pipeline state, private to each role and carried across tiles and rounds.
@@ -207,6 +223,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     uint32_t acc = 0, acc_phase = 0;    // MMA / epilogue accumulators
     int pend[MAX_STAGES];               // producer: parity + 1 of a load not yet released
     for (int s = 0; s < MAX_STAGES; ++s) pend[s] = 0;
+    unsigned int issued = 0, consumed = 0;   // producer / MMA thread: ring stages so far
     const uint32_t idesc = idesc_f16(PREC == SP2_BF16_SPLIT ? 1u : 0u, C::TILE_M);
 
     unsigned int target = 0;
@@ -270,7 +287,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             am = bm = (kb & 1) ? X3 + 2 : X3 + 1;
                         }
                         if (!mbar_wait(&tl.empty[stage], phase ^ 1u, abort, p.timeout_ns, p.err)) {
-                            rc.abort = 1;
+                            tc_abort<CG>(rc, peer_abort);
                             break;
                         }
                         pend[stage] = 0;
@@ -288,6 +305,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             tma_load_2d_pair(sa + C::A_BYTES, bm, kx, row_b, fb);
                         }
                         pend[stage] = (int)phase + 1;
+                        *(volatile unsigned int *)&tl.issued = ++issued;
                         if (++stage == C::STAGES) {
                             stage = 0;
                             phase ^= 1u;
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     const TileWork w = describe(rc, p, g);
                     const InstDesc &d = p.inst[w.inst];
                     if (!mbar_wait(&tl.tempty[acc], acc_phase ^ 1u, abort, p.timeout_ns, p.err)) {
-                        rc.abort = 1;
+                        tc_abort<CG>(rc, peer_abort);
                         break;
                     }
                     tc_fence_after();
@@ -315,10 +333,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             uint32_t sh, sl;
                             const uint32_t st_h = stage;
                             if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                rc.abort = 1;
+                                tc_abort<CG>(rc, peer_abort);
                                 ok = false;
                                 break;
                             }
+                            *(volatile unsigned int *)&tl.consumed = ++consumed;
                             sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
                             if (++stage == C::STAGES) {
                                 stage = 0;
@@ -326,10 +345,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             }
                             const uint32_t st_l = stage;
                             if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                rc.abort = 1;
+                                tc_abort<CG>(rc, peer_abort);
                                 ok = false;
                                 break;
                             }
+                            *(volatile unsigned int *)&tl.consumed = ++consumed;
                             sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
                             if (++stage == C::STAGES) {
                                 stage = 0;
@@ -361,10 +381,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             for (int pr = 0; pr < 2; ++pr) {
                                 const uint32_t st_h = stage;
                                 if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                    rc.abort = 1;
+                                    tc_abort<CG>(rc, peer_abort);
                                     ok = false;
                                     break;
                                 }
+                                *(volatile unsigned int *)&tl.consumed = ++consumed;
                                 const uint32_t sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
                                 if (++stage == C::STAGES) {
                                     stage = 0;
@@ -372,10 +393,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 }
                                 const uint32_t st_l = stage;
                                 if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                    rc.abort = 1;
+                                    tc_abort<CG>(rc, peer_abort);
                                     ok = false;
                                     break;
                                 }
+                                *(volatile unsigned int *)&tl.consumed = ++consumed;
                                 const uint32_t sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
                                 if (++stage == C::STAGES) {
                                     stage = 0;
@@ -627,26 +649,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     }
 
     // ------------------------------ teardown ------------------------------
-    if (warp == 0 && lane == 0 && rc.abort && leader) {
-        // Let loads still in flight land before the CTA (pair) exits: bounded
-        // waits on the barriers that count them (the even CTA's for a pair).
+    // After an abort: MMAs this launch issued complete before tensor memory and the
+    // stages are released (the commit covers every earlier MMA of the issuing thread).
+    if (warp == 1 && lane == 0 && leader && rc.abort) {
+        umma_commit<CG>(&tl.drain);
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(&tl.drain, 0u) && global_ns() - t0 < p.timeout_ns) {
+        }
+    }
+    if (CG == 1 && warp == 0 && lane == 0 && rc.abort) {
+        // Let loads still in flight land before the CTA exits: bounded waits on the
+        // barriers that count them.
         for (int s = 0; s < C::STAGES; ++s) {
             if (pend[s]) {
                 const unsigned long long t0 = global_ns();
-                while (!mbar_try_wait(&tl.full[s], (uint32_t)(pend[s] - 1)) && global_ns() - t0 < 50000000ull) {
+                while (!mbar_try_wait(&tl.full[s], (uint32_t)(pend[s] - 1)) && global_ns() - t0 < p.timeout_ns) {
                 }
             }
         }
     }
-    if (CG == 2 && rc.abort && threadIdx.x == 0) {
-        // The odd CTA's loads complete on its peer's barriers, which it cannot
-        // wait on: give any copy still in flight time to land (bounded, 1 ms).
-        const unsigned long long t0 = global_ns();
-        while (global_ns() - t0 < 1000000ull) {
-        }
-    }
     __syncthreads();
-    if (CG == 2) cluster_sync_all();  // neither CTA leaves while its peer may still signal it
+    if (CG == 2) {
+        cluster_sync_all();   // both CTAs' producers have stopped issuing copies
+        if (threadIdx.x == 0 && leader) {
+            // Copies of either CTA land on the even CTA's full barriers, which count
+            // both CTAs' bytes of a stage (equal shares).  Every ring stage in
+            // [consumed, max(issued)) may still have copies in flight: arm the barrier
+            // for the odd CTA's share if only the odd CTA issued that stage, retire the
+            // odd CTA's share if only this CTA did, then wait (bounded) for the phase.
+            unsigned int odd_issued;
+            const uint32_t odd_addr = cluster_addr(&tl.issued, 1);
+            asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(odd_issued) : "r"(odd_addr) : "memory");
+            const unsigned int own = tl.issued, done = tl.consumed;
+            const unsigned int top = own > odd_issued ? own : odd_issued;
+            for (unsigned int i = done; i < top; ++i) {
+                const uint32_t slot = i % C::STAGES, ph = (i / C::STAGES) & 1u;
+                if (i >= own) mbar_expect_tx(&tl.full[slot], C::STAGE_BYTES);
+                else if (i >= odd_issued)
+                    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(
+                                     smem_u32(&tl.full[slot])),
+                                 "r"(C::STAGE_BYTES)
+                                 : "memory");
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try_wait(&tl.full[slot], ph) && global_ns() - t0 < p.timeout_ns) {
+                }
+            }
+        }
+        __syncthreads();
+        cluster_sync_all();  // neither CTA leaves while its peer may still signal it
+    }
     if (warp == 1) {
         tc_fence_after();
         if (CG == 2)
