@@ -68,3 +68,22 @@ def gather_records(records: dict, world: int):
     for p in parts:
         merged.update(p)
     return merged
+
+
+def run_sharded_batch(sizes: Sequence[int], solve, rank: int, world: int, device=None):
+    """One batch over ``world`` ranks: this rank solves its LPT share and every rank
+    ends with all instances' records.
+
+    ``solve(indices)`` solves the given instances on this rank (one grouped launch
+    on its GPU) and returns ({index: record}, ms, work), ``work`` in whatever unit
+    the rate is quoted in (flops).  Returns (records of every instance, this rank's
+    indices, the slowest rank's ms, the work of all ranks): the whole-job rate is
+    work / ms.  The data path has no collective; only these scalars and records
+    cross ranks."""
+    mine = shard_instances(sizes, rank, world)
+    records, ms, work = solve(mine)
+    if set(records) != set(mine):
+        raise ValueError("solve() must return one record per assigned instance")
+    ms_all, work_all = aggregate_step_time(ms, work, device=device)
+    merged = gather_records(records, world)
+    return merged, mine, ms_all, work_all

@@ -71,3 +71,56 @@ def test_gloo_world_size_two():
     assert val0 == val1 == 300.0
     assert keys0 == keys1 == list(range(6))
     assert owner0 == owner1 and all(owner0[i] == 0 for i in mine0)
+
+
+def _batch_worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sizes = inputs.batch_sizes(64, inputs.rng_for(2, 10_000))
+
+        def solve(idx):
+            # stand-in for one grouped launch: L = 30 layers each, time proportional to the work
+            recs = {i: {"n": sizes[i], "layers": 30, "rank": rank} for i in idx}
+            work = sum(30 * 2.0 * sizes[i] ** 3 for i in idx)
+            return recs, work / 1e12, work
+
+        merged, mine, ms, work = shard.run_sharded_batch(sizes, solve, rank, world)
+        out[rank] = (sorted(mine), ms, work, {i: (r["n"], r["rank"]) for i, r in merged.items()})
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_batch_runner_gloo_world_size_two():
+    """The 64-instance batch across two ranks: a disjoint LPT split, every record on
+    both ranks, the slowest rank's time and the sum of the work."""
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_batch_worker, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    sizes = inputs.batch_sizes(64, inputs.rng_for(2, 10_000))
+    (m0, ms0, w0, rec0), (m1, ms1, w1, rec1) = res[0], res[1]
+    assert sorted(m0 + m1) == list(range(64)) and not set(m0) & set(m1)
+    total = sum(30 * 2.0 * n ** 3 for n in sizes)
+    assert w0 == w1 == pytest.approx(total)
+    loads = [sum(30 * 2.0 * sizes[i] ** 3 for i in m) / 1e12 for m in (m0, m1)]
+    assert ms0 == ms1 == pytest.approx(max(loads))
+    assert rec0 == rec1 and sorted(rec0) == list(range(64))
+    assert all(rec0[i] == (sizes[i], 0) for i in m0) and all(rec0[i] == (sizes[i], 1) for i in m1)
+    # LPT keeps the two ranks' shares within one largest instance of each other
+    assert abs(loads[0] - loads[1]) <= 30 * 2.0 * max(sizes) ** 3 / 1e12
+
+
+def test_sharded_batch_runner_rejects_missing_records():
+    with pytest.raises(ValueError):
+        shard.run_sharded_batch([128, 256], lambda idx: ({}, 1.0, 1.0), 0, 1)
