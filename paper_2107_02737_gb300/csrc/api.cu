@@ -392,6 +392,9 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         d.np = np;
         d.ntiles = (int)tiles[i].size();
         d.parts = d.ntiles * (pl.path == PATH_TC ? pl.cg : 1);
+        // A device constant, so that an instance's tiles walk K the same way in a
+        // batch as alone (the accumulation order, and so the bits, follow the tile).
+        d.kwave = (pl.path == PATH_TC) ? std::max(1, P.grid / pl.cg) : 1;
         d.tile_off = (int)h_tiles.size();
         h_tiles.insert(h_tiles.end(), tiles[i].begin(), tiles[i].end());
         d.n_occ = sp.n_occ;

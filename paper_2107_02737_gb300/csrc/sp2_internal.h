@@ -77,7 +77,8 @@ struct InstCtl {
 struct InstDesc {
     int n, np, ntiles, tile_off;      // tiles: this instance's slice of the tile table
     int parts;                        // partial records per layer (tiles x CTAs per tile)
-    int pad_parts;
+    int kwave;                        // tensor-core path: tiles the device runs at once; tile t walks K
+                                      // upward when (t / kwave) is even, downward when odd
     double n_occ;
     int nforced, nslots_x;            // nforced < 0: decide on device; nslots_x: 2, L+1 or K+s-1
     int ckpt_s, ckpt_k;               // adjoint checkpointing: every s-th X kept (K of them), 0 = off

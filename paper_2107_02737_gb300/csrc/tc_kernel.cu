@@ -262,6 +262,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     const TileWork w = describe(rc, p, g);
                     const InstDesc &d = p.inst[w.inst];
                     const int nkb = d.np / TC_BK;
+                    // Successive waves of tiles walk K in opposite directions, so that a
+                    // wave starts on the K blocks the previous one left in L2.
+                    const bool kdown = ((w.tile / d.kwave) & 1) != 0;
                     const int row_a = w.bi * C::TILE_M + (int)rank * 128;
                     const int row_b = w.bj * TC_BN + (CG == 2 ? (int)rank * 128 : 0);
                     // Square tiles: each K block in two consecutive ring slots, (hi, hi) then
@@ -278,12 +281,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                             // side -- feeding X Y^T and Y X^T.
                             const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
                             const int q = kb & 3;
-                            kx = (kb >> 2) * TC_BK;
+                            kx = (kdown ? nkb - 1 - (kb >> 2) : (kb >> 2)) * TC_BK;
                             const CUtensorMap *xm = (q & 1) ? X3 + 2 : X3 + 1, *ym = (q & 1) ? Y3 + 2 : Y3 + 1;
                             am = (q < 2) ? xm : ym;
                             bm = (q < 2) ? ym : xm;
                         } else {
-                            kx = (kb >> 1) * TC_BK;
+                            kx = (kdown ? nkb - 1 - (kb >> 1) : (kb >> 1)) * TC_BK;
                             am = bm = (kb & 1) ? X3 + 2 : X3 + 1;
                         }
                         if (!mbar_wait(&tl.empty[stage], phase ^ 1u, abort, p.timeout_ns, p.err)) {
@@ -484,17 +487,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 double dw = 0.0;
                 if (ok && rw0 < np) {
 #pragma unroll 1
-                    for (int j = 0; j < 128 / EPI_CHUNK; ++j) {
+                    // The chunks this warp finishes form one range [j0, j1): chunks entirely
+                    // below the diagonal come first, chunks past np last.
+                    int j0 = 0, j1 = 128 / EPI_CHUNK;
+                    while (j1 > 0 && w.bj * TC_BN + half * 128 + (j1 - 1) * EPI_CHUNK >= np) --j1;
+                    while (j0 < j1 && w.bj * TC_BN + half * 128 + j0 * EPI_CHUNK + EPI_CHUNK - 1 < rw0) ++j0;
+                    // The previous layer's (r, c) values -- (c, r) by symmetry, coalesced across
+                    // the warp, evict-first -- are loaded one chunk ahead, so that their latency
+                    // overlaps the current chunk's arithmetic and stores.
+                    float xnx[EPI_CHUNK];
+                    if (j0 < j1) {
+                        const int cb0 = w.bj * TC_BN + half * 128 + j0 * EPI_CHUNK;
+#pragma unroll
+                        for (int jj = 0; jj < EPI_CHUNK; ++jj) xnx[jj] = __ldcs(old + (size_t)(cb0 + jj) * np + r);
+                    }
+#pragma unroll 1
+                    for (int j = j0; j < j1; ++j) {
                         const int c0 = half * 128 + j * EPI_CHUNK;   // column offset in the tile
                         const int cb = w.bj * TC_BN + c0;
-                        if (cb >= np) break;
-                        if (cb + EPI_CHUNK - 1 < rw0) continue;  // chunk entirely below the diagonal
-                        // All loads of the previous layer's (r, c) values are issued before
-                        // any store of this chunk: (c, r) by symmetry, coalesced across the
-                        // warp, evict-first.
                         float xov[EPI_CHUNK];
 #pragma unroll
-                        for (int jj = 0; jj < EPI_CHUNK; ++jj) xov[jj] = __ldcs(old + (size_t)(cb + jj) * np + r);
+                        for (int jj = 0; jj < EPI_CHUNK; ++jj) xov[jj] = xnx[jj];
+                        if (j + 1 < j1) {
+#pragma unroll
+                            for (int jj = 0; jj < EPI_CHUNK; ++jj)
+                                xnx[jj] = __ldcs(old + (size_t)(cb + EPI_CHUNK + jj) * np + r);
+                        }
                         float v[EPI_CHUNK];
                         tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + c0, v);
                         // Each element's next split operands are computed once, stored to the
