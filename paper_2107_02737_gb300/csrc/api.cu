@@ -168,12 +168,40 @@ int init_blocks_host(int np) { return np < INIT_BLOCKS_MAX ? np : INIT_BLOCKS_MA
 
 struct Plan {
     int mode, path, precision;
+    bool dataflow = false;            // see flow_eligible
     int cg = 1;                       // CTAs per tensor-core tile
     std::vector<InstSpec> inst;       // non-trivial instances, in launch order
     std::vector<int> slots;           // nslots_x per instance
     std::vector<int> ckpt_s, ckpt_k;  // adjoint checkpoint stride and kept layers (0: every layer kept)
     int max_np = 0, max_n = 0;
 };
+
+// The dataflow schedule of the tensor-core kernel (no grid barrier between layers)
+// serves one instance in density mode; it keeps three operand slots, so that a layer's
+// operands are not overwritten while a slow CTA may still load them.
+bool flow_eligible(const Plan &pl) { return pl.mode == MODE_DENSITY && pl.path == PATH_TC && pl.inst.size() == 1; }
+void set_flow(Plan &pl) {
+    pl.dataflow = flow_eligible(pl);
+    if (pl.dataflow) pl.slots[0] = 3;
+}
+
+// Blocks of 256 x 256 of an np x np X and, per block, the (at most two) tiles that
+// write its elements, directly or as mirrors; -1 where none.
+int flow_nblk(int np) { return (np + 255) / 256; }
+void build_block_sources(int np, int cg, const std::vector<int2> &tiles, std::vector<int> &src) {
+    const int nb = flow_nblk(np), bm = TC_BM * cg;
+    src.assign((size_t)nb * nb * 2, -1);
+    auto add = [&](int P, int Q, int t) {
+        int *e = &src[((size_t)P * nb + Q) * 2];
+        if (e[0] < 0) e[0] = t;
+        else if (e[1] < 0 && e[0] != t) e[1] = t;
+    };
+    for (int t = 0; t < (int)tiles.size(); ++t) {
+        const int P = tiles[t].x * bm / 256, Q = tiles[t].y;
+        add(P, Q, t);
+        if (P != Q) add(Q, P, t);
+    }
+}
 
 // Operand storage of an adjoint whose forward chain has at most `lmax` layers:
 // every X_n (lmax + 1 slots), or with checkpoint stride s the K = lmax/s + 1 kept
@@ -221,6 +249,11 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
         const int cap = std::max(parts_for(pl.path, np, pl.cg), initb);
         c.take(sizeof(Part) * cap);
         c.take(sizeof(Part) * cap);
+        c.take(sizeof(Part) * cap);
+        if (pl.dataflow) {
+            c.take(sizeof(unsigned int) * ntiles_for(pl.path, np, pl.cg));      // tile completions
+            c.take(sizeof(int) * 2 * (size_t)flow_nblk(np) * flow_nblk(np));  // block sources
+        }
         c.take(sizeof(double2) * FIN_BLOCKS_MAX);
         c.take(mat * 4);
         c.take(mat * 4);
@@ -310,7 +343,10 @@ struct Prepared {
     bool user_bounds = false;
     InstDesc *d_inst = nullptr;
     int2 *d_tiles = nullptr;
-    uint8_t *d_sync = nullptr;
+    uint8_t *d_sync = nullptr;       // grid barrier counter, error word, dataflow layer counter
+    unsigned int *d_tile_done = nullptr;   // dataflow: per-tile completion counters
+    int *d_blk_src = nullptr;              // dataflow: block sources
+    int flow_tiles = 0, flow_nb = 0;
     InstCtl *d_ctl = nullptr;        // B live control blocks
     InstCtl *d_ctl_init = nullptr;   // B initial control blocks
     std::vector<InstCtl> h_ctl;
@@ -405,6 +441,16 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         d.ctl = d_ctl + i;
         d.part[0] = (Part *)c.take(sizeof(Part) * d.part_cap);
         d.part[1] = (Part *)c.take(sizeof(Part) * d.part_cap);
+        d.part[2] = (Part *)c.take(sizeof(Part) * d.part_cap);
+        if (pl.dataflow) {
+            P.flow_tiles = d.ntiles;
+            P.flow_nb = flow_nblk(np);
+            P.d_tile_done = (unsigned int *)c.take(sizeof(unsigned int) * d.ntiles);
+            P.d_blk_src = (int *)c.take(sizeof(int) * 2 * (size_t)P.flow_nb * P.flow_nb);
+            std::vector<int> src;
+            build_block_sources(np, pl.cg, tiles[i], src);
+            CK(cudaMemcpyAsync(P.d_blk_src, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, s));
+        }
         d.fin_part = (double2 *)c.take(sizeof(double2) * FIN_BLOCKS_MAX);
         d.xf[0] = (float *)c.take(mat * 4);
         d.xf[1] = (float *)c.take(mat * 4);
@@ -585,6 +631,7 @@ sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
     const int B = (int)pl.inst.size();
     CK(cudaMemcpyAsync(P.d_ctl, P.d_ctl_init, sizeof(InstCtl) * B, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(P.d_sync, 0, 64, s));
+    if (pl.dataflow) CK(cudaMemsetAsync(P.d_tile_done, 0, sizeof(unsigned int) * P.flow_tiles, s));
     if (ev) CK(cudaEventRecord(ev[0], s));
     if (pl.mode == MODE_APPLY) {
         CK(launch_init_x_from(P.d_inst, pl.inst[0].X0, pl.max_np, pl.path, pl.precision, s));
@@ -610,6 +657,13 @@ sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
     rp.max_layers = P.o.max_layers;
     // Device hook: CTA 0 withholds its first barrier arrival (test_hook 1, or 3 in a CTA-pair launch).
     rp.test_hook = (P.o.test_hook == 1 || (P.o.test_hook == 3 && pl.path == PATH_TC && pl.cg == 2)) ? 1 : 0;
+    if (pl.dataflow) {
+        rp.dataflow = 1;
+        rp.nblk = P.flow_nb;
+        rp.tile_done = P.d_tile_done;
+        rp.layer_done = (unsigned int *)(P.d_sync + 8);
+        rp.blk_src = P.d_blk_src;
+    }
     if (ev) CK(cudaEventRecord(ev[1], s));
     CK(pl.path == PATH_TC ? launch_tc_persistent(rp, pl.cg, P.grid, s) : launch_simt_persistent(rp, P.grid, s));
     if (ev) CK(cudaEventRecord(ev[2], s));
@@ -812,6 +866,7 @@ sp2_status run_instances(int mode, std::vector<InstSpec> &specs, double tol, con
         pl.max_n = std::max(pl.max_n, sp.n);
         pl.max_np = std::max(pl.max_np, round_up(sp.n, PAD));
     }
+    set_flow(pl);
     r = run_plan(pl, tol, o, ws, ws_bytes, s);
     if (status_rank(r) > status_rank(worst)) worst = r;
     return (sp2_status)worst;
@@ -837,6 +892,7 @@ size_t bytes_for(int mode, const std::vector<int> &ns, int layers, const sp2_opt
         pl.max_np = std::max(pl.max_np, round_up(n, PAD));
     }
     if (pl.inst.empty()) return 0;
+    set_flow(pl);
     pl.cg = 1;
     const size_t b1 = plan_bytes(pl);
     pl.cg = 2;
@@ -964,6 +1020,7 @@ sp2_status sp2_batch_plan_create(int B, const double *const *H, const int *N, co
         pl.max_n = std::max(pl.max_n, sp.n);
         pl.max_np = std::max(pl.max_np, round_up(sp.n, PAD));
     }
+    set_flow(pl);
     pb->order = order;
     if (!pl.inst.empty()) {
         // Workspace for either tile shape, owned by the plan.

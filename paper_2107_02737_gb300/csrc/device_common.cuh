@@ -192,6 +192,7 @@ struct RoundCtl {
     float chist_a[MAX_L + 2];        // adjoint (B = 1): a_n of the layer that produced X_n
     float alpha[MAX_BATCH];          // a of the layer computed this round (1 = plain)
     float xl[MAX_BATCH], xh[MAX_BATCH];  // accelerated chain: images of eps_lumo, eps_homo
+    int flow_go;                     // dataflow schedule: the previous layer is complete
 };
 
 __host__ __device__ __forceinline__ int layer_rule(double t, double q, double n_occ) {
@@ -243,27 +244,36 @@ __device__ __forceinline__ void round_ctl_init(RoundCtl &rc, const RunParams &p)
 // entries l, l + 32, ... in increasing order, then a fixed shuffle tree.  The
 // order depends only on the instance's own partials, so every CTA -- and a batch
 // or a lone call alike -- gets the same bits and takes the same decision.
+// One warp: the sums of instance i's partials of the layer just finished, lane l
+// adding entries l, l + 32, ... in increasing order, then a fixed shuffle tree
+// (valid in lane 0).
+__device__ __forceinline__ void sum_instance_partials(const RoundCtl &rc, const RunParams &p, int i, int lane,
+                                                      double (&a)[4]) {
+    const InstDesc &d = p.inst[i];
+    const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
+    const int cnt = (n == 0) ? d.ctl->init_parts : d.parts;
+    const Part *part = d.part[n % 3];
+    a[0] = a[1] = a[2] = a[3] = 0.0;
+#pragma unroll 4
+    for (int k = lane; k < cnt; k += 32) {
+        const Part v = part[k];
+        a[0] += v.t;
+        a[1] += v.q;
+        a[2] += v.w;
+        a[3] += v.p;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+}
+
 __device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams &p, double *sums) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (rc.phase == 1) return;
     for (int i = wid; i < p.B; i += nw) {
         if (!rc.active[i]) continue;
-        const InstDesc &d = p.inst[i];
-        const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
-        const int cnt = (n == 0) ? d.ctl->init_parts : d.parts;
-        const Part *part = d.part[n & 1];
-        double a[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
-        for (int k = lane; k < cnt; k += 32) {
-            const Part v = part[k];
-            a[0] += v.t;
-            a[1] += v.q;
-            a[2] += v.w;
-            a[3] += v.p;
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+        double a[4];
+        sum_instance_partials(rc, p, i, lane, a);
         if (lane == 0)
             for (int c = 0; c < 4; ++c) sums[i * 4 + c] = a[c];
     }
@@ -502,7 +512,7 @@ __device__ inline void reduce_round_partials_block(const RoundCtl &rc, const Run
         const InstDesc &d = p.inst[i];
         const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
         const int cnt = (n == 0) ? d.ctl->init_parts : d.parts;
-        const Part *part = d.part[n & 1];
+        const Part *part = d.part[n % 3];
         double a[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 4
         for (int k = tid; k < cnt; k += blockDim.x) {

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(SIMT_THREADS) k_simt_persistent(const __grid_c
                     s.t += sm.red[w][0];
                     s.q += sm.red[w][1];
                 }
-                d.part[(n + 1) & 1][tile] = s;
+                d.part[(n + 1) % 3][tile] = s;
             }
             __syncthreads();
         }

@@ -13,8 +13,11 @@
 //               X_{(K-1)s} (with FP32 masters in ckf), slots K..K+s-2 the others
 //               by n mod s; the reverse sweep recomputes a segment's layers from
 //               its kept X into those slots (FP32 ping-pong rf).
-//   part[2]     FP64 partials per tile, ping-pong by layer parity: Tr X, ||X||_F^2,
+//   part[3]     FP64 partials per tile, by layer n mod 3: Tr X, ||X||_F^2,
 //               ||Y||_F^2 and Tr P (see Part).
+//   dataflow schedule (one instance, density mode, tensor cores): three operand
+//               slots; per tile a completion counter (CTAs done, all layers) and a
+//               table of the tiles that write each 256 x 256 block of X.
 // Tensor-core path: the operands are the split of Y = X - I/2 (identity on the
 // first N diagonal entries only), and the true X_n is the stored FP32 X_n plus
 // c_n I, where the scalar c_n removes the measured accumulator bias of the
@@ -93,7 +96,7 @@ struct InstDesc {
     uint16_t *xop;                    // slot s: hi at xop + 2 s np^2, lo at xop + (2 s + 1) np^2
     float *yf[2];
     uint16_t *yop;                    // slot s in {0,1}: hi, lo as for xop
-    Part *part[2];
+    Part *part[3];                    // by layer n mod 3 (three deep for the dataflow schedule)
     int part_cap, fin_blocks;
     const CUtensorMap *xmap;          // [nslots_x * 3]: per slot the K segments' op0, op1, op2 = hi, hi, lo
     const CUtensorMap *ymap;          // [2 * 3]
@@ -113,7 +116,13 @@ struct RunParams {
     double tol;
     unsigned long long timeout_ns;
     int B, mode, precision, max_layers;
-    int test_hook;                    // 1: CTA 0 withholds its first barrier arrival
+    int test_hook;                    // 1: CTA 0 withholds its first barrier arrival (dataflow:
+                                      // its first tile completion)
+    int dataflow;                     // 1: no grid barrier between layers (see the tensor-core kernel)
+    int nblk;                         // dataflow: 256-row blocks of X (round_up(np, 256) / 256)
+    unsigned int *tile_done;          // dataflow: per tile, CTA completions over all layers
+    unsigned int *layer_done;         // dataflow: CTA-tile completions over all layers
+    const int *blk_src;               // dataflow: [nblk * nblk * 2] tiles writing block (P, Q) of X, -1 none
 };
 
 // Host-side launchers (one translation unit each).

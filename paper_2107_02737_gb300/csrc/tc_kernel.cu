@@ -156,6 +156,114 @@ __device__ __forceinline__ TileWork describe(const RoundCtl &rc, const RunParams
     return w;
 }
 
+// Dataflow schedule: tile g of layer r for the producer and the MMA thread (the
+// layer's sign and offset are not needed there).
+__device__ __forceinline__ TileWork describe_flow(const RunParams &p, int g, int r) {
+    TileWork w;
+    const InstDesc &d = p.inst[0];
+    const int2 bt = p.tiles[d.tile_off + g];
+    w.inst = 0;
+    w.job = 0;
+    w.tile = g;
+    w.bi = bt.x;
+    w.bj = bt.y;
+    w.resp = 0;
+    w.xslot = xslot_of(d, r);
+    w.ybuf = 0;
+    w.flip = 0;
+    w.n = r;
+    w.rec = 0;
+    w.cf = 0.0f;
+    w.alpha = 1.0f;
+    return w;
+}
+
+// Dataflow schedule, producer.  A 256-column block kt of the operand row blocks pa
+// and pb of X_n was written by at most four tiles of the previous layer, each done
+// when its counter reaches `target` (CG completions per layer).  The counters are
+// read with relaxed loads one block ahead (flow_peek), so their latency hides under
+// the current block's copies, and re-polled only while a tile is still running;
+// one acquire fence then orders the TMA reads after the tiles' stores.
+__device__ __forceinline__ unsigned int ld_relaxed(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void flow_peek(const RunParams &p, int pa, int pb, int kt, unsigned int (&v)[4]) {
+    const int *e0 = p.blk_src + (pa * p.nblk + kt) * 2, *e1 = p.blk_src + (pb * p.nblk + kt) * 2;
+    const int src[4] = {e0[0], e0[1], e1[0], e1[1]};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = src[k] < 0 ? 0xFFFFFFFFu : ld_relaxed(p.tile_done + src[k]);
+}
+__device__ __noinline__ bool flow_wait(const RunParams &p, int pa, int pb, int kt, unsigned int target,
+                                       unsigned int (&v)[4], const volatile int *abort) {
+    const int *e0 = p.blk_src + (pa * p.nblk + kt) * 2, *e1 = p.blk_src + (pb * p.nblk + kt) * 2;
+    const int src[4] = {e0[0], e0[1], e1[0], e1[1]};
+    const unsigned long long t0 = global_ns();
+    for (int k = 0; k < 4; ++k) {
+        while (v[k] < target) {
+            if (*abort || ld_volatile(p.err) != 0) return false;
+            if (global_ns() - t0 > p.timeout_ns) {
+                set_error(p.err, SP2_ERR_TIMEOUT);
+                return false;
+            }
+            __nanosleep(32);
+            v[k] = ld_relaxed(p.tile_done + src[k]);
+        }
+    }
+    // The tiles' generic-proxy stores, released with their counters, reach the TMA reads.
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return true;
+}
+
+// Dataflow schedule, the eight epilogue warps: wait for every CTA-tile of layer r - 1
+// (`per_layer` completions each), then the same sums in the same order as the
+// barrier schedule (one warp) and the same decision for instance 0.  Returns false
+// when the chain stopped or the launch is stopping.  `sums` is four doubles of
+// shared memory.
+__device__ __noinline__ bool flow_decide(RoundCtl &rc, const RunParams &p, double *sums, int r, int ew, int lane,
+                                         unsigned int per_layer, const volatile int *abort) {
+    if (ew == 0 && lane == 0) {
+        int go = 1;
+        if (r > 0) {
+            const unsigned int target = per_layer * (unsigned int)r;
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire(p.layer_done) < target) {
+                if (*abort || ld_volatile(p.err) != 0) {
+                    go = 0;
+                    break;
+                }
+                if (global_ns() - t0 > p.timeout_ns) {
+                    set_error(p.err, SP2_ERR_TIMEOUT);
+                    go = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (ld_volatile(p.err) != 0) go = 0;
+        rc.flow_go = go;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
+    if (!rc.flow_go) return false;
+    if (ew == 0) {
+        double a[4];
+        sum_instance_partials(rc, p, 0, lane, a);
+        if (lane == 0)
+            for (int c = 0; c < 4; ++c) sums[c] = a[c];
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
+    if (ew == 0 && lane == 0) {
+        const int width = decide_instance(rc, p, sums, 0, blockIdx.x == 0);
+        rc.prefix[0] = 0;
+        rc.prefix[1] = width;
+        rc.total = width;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
+    return rc.total > 0;
+}
+
 template <int PREC, int CG>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_constant__ RunParams p) {
     using C = Cfg<CG>;
@@ -226,443 +334,544 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     unsigned int issued = 0, consumed = 0;   // producer / MMA thread: ring stages so far
     const uint32_t idesc = idesc_f16(PREC == SP2_BF16_SPLIT ? 1u : 0u, C::TILE_M);
 
-    unsigned int target = 0;
-    bool first = true;
-    while (true) {
-        if (!first) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const bool withhold = (p.test_hook == 1 && blockIdx.x == 0 && target == 0);
-                target += gridDim.x;
-                if (!grid_barrier(p.barrier, target, p.err, p.timeout_ns, withhold)) rc.abort = 1;
+    // ---------- per-tile work of the three roles (both schedules below) ----------
+    // Producer: every K block of tile w into the ring.  In the dataflow schedule a
+    // 256-column block of X_n is loaded only once the tiles of the previous layer
+    // that wrote it (and its mirror) have completed.
+    int df_round = -1;   // dataflow: layer whose inputs are known to be complete everywhere
+    auto produce_tile = [&](const TileWork &w) {
+        // Dataflow: the column block checked last, the one peeked ahead and its counters.
+        int df_kt = -1, df_next = -1;
+        unsigned int df_v[4] = {0u, 0u, 0u, 0u};
+        bool df_ready = !p.dataflow || w.n == 0 || df_round == w.n;
+        if (!df_ready) {
+            if (ld_relaxed(p.layer_done) >= (unsigned int)(CG * p.inst[0].ntiles * w.n)) {
+                df_round = w.n;   // every tile of the previous layer is done
+                df_ready = true;
+            } else {
+                // Or every tile that wrote this tile's two operand row blocks is: one pass
+                // of relaxed loads (all in flight together), no per-block checks then.
+                const int pa = (w.bi * C::TILE_M + (int)rank * 128) / 256, pb = w.bj;
+                const int nb = (p.inst[0].np + 255) / 256;
+                unsigned int mn = 0xFFFFFFFFu;
+                for (int kt = 0; kt < nb; ++kt) {
+                    unsigned int v[4];
+                    flow_peek(p, pa, pb, kt, v);
+                    mn = min(mn, min(min(v[0], v[1]), min(v[2], v[3])));
+                }
+                df_ready = mn >= (unsigned int)(CG * w.n);
             }
-            __syncthreads();
-            if (rc.abort) break;
+            if (df_ready) {
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
         }
-        first = false;
-        // The epilogue transpose buffers are idle here: use them for the sums.
-        reduce_round_partials(rc, p, (double *)epi_T);
-        if (p.mode == MODE_ADJOINT) {
-            if (threadIdx.x == 0) decide_round(rc, p, (const double *)epi_T);
-        } else {
-            decide_round_parallel(rc, p, (const double *)epi_T, (int *)((double *)epi_T + 4 * MAX_BATCH));
-        }
-        if (threadIdx.x == 0) {
-            // Make the previous round's global writes (other CTAs' epilogues,
-            // generic proxy) visible to this CTA's TMA reads (async proxy).
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-        }
-        __syncthreads();
-        if (rc.abort || rc.total == 0) break;
-
-        if (warp == 0) {
-            // ------------------------- TMA producer -------------------------
-            if (lane == 0) {
-                for (int g = cluster_id; g < rc.total && !*abort; g += nclusters) {
-                    const TileWork w = describe(rc, p, g);
-                    const InstDesc &d = p.inst[w.inst];
-                    const int nkb = d.np / TC_BK;
-                    // Successive waves of tiles walk K in opposite directions, so that a
-                    // wave starts on the K blocks the previous one left in L2.
-                    const bool kdown = ((w.tile / d.kwave) & 1) != 0;
-                    const int row_a = w.bi * C::TILE_M + (int)rank * 128;
-                    const int row_b = w.bj * TC_BN + (CG == 2 ? (int)rank * 128 : 0);
-                    // Square tiles: each K block in two consecutive ring slots, (hi, hi) then
-                    // (lo, lo), which feed all three products.  Response tiles: the six
-                    // segments one after another, one K block per slot.
-                    const int nslot = (w.resp ? 4 : 2) * nkb;
-                    const CUtensorMap *X3 = d.xmap + w.xslot * 3;   // maps hi, hi, lo
-                    for (int kb = 0; kb < nslot; ++kb) {
-                        int kx;
-                        const CUtensorMap *am, *bm;
-                        if (w.resp) {
-                            // Response / adjoint tiles: per K block (X hi, Y hi), (X lo, Y lo),
-                            // (Y hi, X hi), (Y lo, X lo) -- rows bi on the A side, rows bj on the B
-                            // side -- feeding X Y^T and Y X^T.
-                            const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
-                            const int q = kb & 3;
-                            kx = (kdown ? nkb - 1 - (kb >> 2) : (kb >> 2)) * TC_BK;
-                            const CUtensorMap *xm = (q & 1) ? X3 + 2 : X3 + 1, *ym = (q & 1) ? Y3 + 2 : Y3 + 1;
-                            am = (q < 2) ? xm : ym;
-                            bm = (q < 2) ? ym : xm;
-                        } else {
-                            kx = (kdown ? nkb - 1 - (kb >> 1) : (kb >> 1)) * TC_BK;
-                            am = bm = (kb & 1) ? X3 + 2 : X3 + 1;
-                        }
-                        if (!mbar_wait(&tl.empty[stage], phase ^ 1u, abort, p.timeout_ns, p.err)) {
-                            tc_abort<CG>(rc, peer_abort);
-                            break;
-                        }
-                        pend[stage] = 0;
-                        uint8_t *sa = stages + (size_t)stage * C::STAGE_BYTES;
-                        if (CG == 1) {
-                            mbar_expect_tx(&tl.full[stage], C::TX_BYTES);
-                            tma_load_2d(sa, am, kx, row_a, &tl.full[stage]);
-                            tma_load_2d(sa + C::A_BYTES, bm, kx, row_b, &tl.full[stage]);
-                            tma_load_2d(sa + C::A_BYTES + C::B_BYTES / 2, bm, kx, row_b + 128, &tl.full[stage]);
-                        } else {
-                            // Both CTAs' bytes complete on the even CTA's barrier.
-                            if (leader) mbar_expect_tx(&tl.full[stage], C::TX_BYTES);
-                            const uint32_t fb = lead_full0 + stage * 8u;
-                            tma_load_2d_pair(sa, am, kx, row_a, fb);
-                            tma_load_2d_pair(sa + C::A_BYTES, bm, kx, row_b, fb);
-                        }
-                        pend[stage] = (int)phase + 1;
-                        *(volatile unsigned int *)&tl.issued = ++issued;
-                        if (++stage == C::STAGES) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
-                    }
+        const InstDesc &d = p.inst[w.inst];
+        const int nkb = d.np / TC_BK;
+        // Successive waves of tiles walk K in opposite directions, so that a
+        // wave starts on the K blocks the previous one left in L2.
+        const bool kdown = ((w.tile / d.kwave) & 1) != 0;
+        const int row_a = w.bi * C::TILE_M + (int)rank * 128;
+        const int row_b = w.bj * TC_BN + (CG == 2 ? (int)rank * 128 : 0);
+        // Square tiles: each K block in two consecutive ring slots, (hi, hi) then
+        // (lo, lo), which feed all three products.  Response tiles: the six
+        // segments one after another, one K block per slot.
+        const int nslot = (w.resp ? 4 : 2) * nkb;
+        const CUtensorMap *X3 = d.xmap + w.xslot * 3;   // maps hi, hi, lo
+        for (int kb = 0; kb < nslot; ++kb) {
+            int kx;
+            const CUtensorMap *am, *bm;
+            if (w.resp) {
+                // Response / adjoint tiles: per K block (X hi, Y hi), (X lo, Y lo),
+                // (Y hi, X hi), (Y lo, X lo) -- rows bi on the A side, rows bj on the B
+                // side -- feeding X Y^T and Y X^T.
+                const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
+                const int q = kb & 3;
+                kx = (kdown ? nkb - 1 - (kb >> 2) : (kb >> 2)) * TC_BK;
+                const CUtensorMap *xm = (q & 1) ? X3 + 2 : X3 + 1, *ym = (q & 1) ? Y3 + 2 : Y3 + 1;
+                am = (q < 2) ? xm : ym;
+                bm = (q < 2) ? ym : xm;
+            } else {
+                kx = (kdown ? nkb - 1 - (kb >> 1) : (kb >> 1)) * TC_BK;
+                am = bm = (kb & 1) ? X3 + 2 : X3 + 1;
+            }
+            if (!df_ready && kx / 256 != df_kt) {
+                // Dataflow: this 256-column block of both operand panels must come
+                // from tiles of the previous layer that have completed.
+                df_kt = kx / 256;
+                const int pa = row_a / 256, pb = row_b / 256;
+                if (df_next != df_kt) flow_peek(p, pa, pb, df_kt, df_v);
+                if (!flow_wait(p, pa, pb, df_kt, (unsigned int)(CG * w.n), df_v, abort)) {
+                    tc_abort<CG>(rc, peer_abort);
+                    break;
+                }
+                const int nx = kdown ? df_kt - 1 : df_kt + 1;   // next block of this walk
+                df_next = -1;
+                if (nx >= 0 && nx * 256 < d.np) {
+                    flow_peek(p, pa, pb, nx, df_v);
+                    df_next = nx;
                 }
             }
-        } else if (warp == 1) {
-            // -------------------------- MMA issuer --------------------------
-            if (lane == 0 && leader) {
-                for (int g = cluster_id; g < rc.total && !*abort; g += nclusters) {
-                    const TileWork w = describe(rc, p, g);
-                    const InstDesc &d = p.inst[w.inst];
-                    if (!mbar_wait(&tl.tempty[acc], acc_phase ^ 1u, abort, p.timeout_ns, p.err)) {
+            if (!mbar_wait(&tl.empty[stage], phase ^ 1u, abort, p.timeout_ns, p.err)) {
+                tc_abort<CG>(rc, peer_abort);
+                break;
+            }
+            pend[stage] = 0;
+            uint8_t *sa = stages + (size_t)stage * C::STAGE_BYTES;
+            if (CG == 1) {
+                mbar_expect_tx(&tl.full[stage], C::TX_BYTES);
+                tma_load_2d(sa, am, kx, row_a, &tl.full[stage]);
+                tma_load_2d(sa + C::A_BYTES, bm, kx, row_b, &tl.full[stage]);
+                tma_load_2d(sa + C::A_BYTES + C::B_BYTES / 2, bm, kx, row_b + 128, &tl.full[stage]);
+            } else {
+                // Both CTAs' bytes complete on the even CTA's barrier.
+                if (leader) mbar_expect_tx(&tl.full[stage], C::TX_BYTES);
+                const uint32_t fb = lead_full0 + stage * 8u;
+                tma_load_2d_pair(sa, am, kx, row_a, fb);
+                tma_load_2d_pair(sa + C::A_BYTES, bm, kx, row_b, fb);
+            }
+            pend[stage] = (int)phase + 1;
+            *(volatile unsigned int *)&tl.issued = ++issued;
+            if (++stage == C::STAGES) {
+                stage = 0;
+                phase ^= 1u;
+            }
+        }
+    };
+    // MMA issuer: tile w's products into the next accumulator; false when a wait
+    // gave up (the launch is stopping).
+    auto mma_tile = [&](const TileWork &w) -> bool {
+        const InstDesc &d = p.inst[w.inst];
+        if (!mbar_wait(&tl.tempty[acc], acc_phase ^ 1u, abort, p.timeout_ns, p.err)) {
+            tc_abort<CG>(rc, peer_abort);
+            return false;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * TC_BN;
+        bool ok = true;
+        if (!w.resp) {
+            // Square: per K block the (hi, hi) and (lo, lo) slots, then hi lo, lo hi
+            // (the small cross terms first) and hi hi.
+            for (int kb = 0; kb < d.np / TC_BK; ++kb) {
+                uint32_t sh, sl;
+                const uint32_t st_h = stage;
+                if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                    tc_abort<CG>(rc, peer_abort);
+                    ok = false;
+                    break;
+                }
+                *(volatile unsigned int *)&tl.consumed = ++consumed;
+                sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                if (++stage == C::STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+                const uint32_t st_l = stage;
+                if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                    tc_abort<CG>(rc, peer_abort);
+                    ok = false;
+                    break;
+                }
+                *(volatile unsigned int *)&tl.consumed = ++consumed;
+                sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                if (++stage == C::STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)   // hi x lo
+                    umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32), sdesc_sw128(sl + C::A_BYTES + k * 32),
+                                 idesc, (kb | k) != 0 ? 1u : 0u);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)   // lo x hi
+                    umma_f16<CG>(d_tmem, sdesc_sw128(sl + k * 32), sdesc_sw128(sh + C::A_BYTES + k * 32),
+                                 idesc, 1u);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)   // hi x hi
+                    umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32), sdesc_sw128(sh + C::A_BYTES + k * 32),
+                                 idesc, 1u);
+                umma_commit<CG>(&tl.empty[st_h]);
+                umma_commit<CG>(&tl.empty[st_l]);
+            }
+        }
+        if (w.resp) {
+            // Response: per K block the slots (X hi, Y hi), (X lo, Y lo) for X Y^T,
+            // released as soon as those products are issued, then (Y hi, X hi),
+            // (Y lo, X lo) for Y X^T; cross terms before hi x hi in each.
+            for (int kb = 0; ok && kb < d.np / TC_BK; ++kb) {
+#pragma unroll 1
+                for (int pr = 0; pr < 2; ++pr) {
+                    const uint32_t st_h = stage;
+                    if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
                         tc_abort<CG>(rc, peer_abort);
+                        ok = false;
                         break;
                     }
+                    *(volatile unsigned int *)&tl.consumed = ++consumed;
+                    const uint32_t sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                    if (++stage == C::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                    const uint32_t st_l = stage;
+                    if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
+                        tc_abort<CG>(rc, peer_abort);
+                        ok = false;
+                        break;
+                    }
+                    *(volatile unsigned int *)&tl.consumed = ++consumed;
+                    const uint32_t sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
+                    if (++stage == C::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + acc * TC_BN;
-                    bool ok = true;
-                    if (!w.resp) {
-                        // Square: per K block the (hi, hi) and (lo, lo) slots, then hi lo, lo hi
-                        // (the small cross terms first) and hi hi.
-                        for (int kb = 0; kb < d.np / TC_BK; ++kb) {
-                            uint32_t sh, sl;
-                            const uint32_t st_h = stage;
-                            if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                tc_abort<CG>(rc, peer_abort);
-                                ok = false;
-                                break;
-                            }
-                            *(volatile unsigned int *)&tl.consumed = ++consumed;
-                            sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
-                            if (++stage == C::STAGES) {
-                                stage = 0;
-                                phase ^= 1u;
-                            }
-                            const uint32_t st_l = stage;
-                            if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                tc_abort<CG>(rc, peer_abort);
-                                ok = false;
-                                break;
-                            }
-                            *(volatile unsigned int *)&tl.consumed = ++consumed;
-                            sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
-                            if (++stage == C::STAGES) {
-                                stage = 0;
-                                phase ^= 1u;
-                            }
-                            tc_fence_after();
 #pragma unroll
-                            for (int k = 0; k < TC_BK / 16; ++k)   // hi x lo
-                                umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32), sdesc_sw128(sl + C::A_BYTES + k * 32),
-                                             idesc, (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < TC_BK / 16; ++k)   // A hi x B lo
+                        umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32),
+                                     sdesc_sw128(sl + C::A_BYTES + k * 32), idesc,
+                                     (kb | pr | k) != 0 ? 1u : 0u);
 #pragma unroll
-                            for (int k = 0; k < TC_BK / 16; ++k)   // lo x hi
-                                umma_f16<CG>(d_tmem, sdesc_sw128(sl + k * 32), sdesc_sw128(sh + C::A_BYTES + k * 32),
-                                             idesc, 1u);
+                    for (int k = 0; k < TC_BK / 16; ++k)   // A lo x B hi
+                        umma_f16<CG>(d_tmem, sdesc_sw128(sl + k * 32),
+                                     sdesc_sw128(sh + C::A_BYTES + k * 32), idesc, 1u);
 #pragma unroll
-                            for (int k = 0; k < TC_BK / 16; ++k)   // hi x hi
-                                umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32), sdesc_sw128(sh + C::A_BYTES + k * 32),
-                                             idesc, 1u);
-                            umma_commit<CG>(&tl.empty[st_h]);
-                            umma_commit<CG>(&tl.empty[st_l]);
-                        }
-                    }
-                    if (w.resp) {
-                        // Response: per K block the slots (X hi, Y hi), (X lo, Y lo) for X Y^T,
-                        // released as soon as those products are issued, then (Y hi, X hi),
-                        // (Y lo, X lo) for Y X^T; cross terms before hi x hi in each.
-                        for (int kb = 0; ok && kb < d.np / TC_BK; ++kb) {
-#pragma unroll 1
-                            for (int pr = 0; pr < 2; ++pr) {
-                                const uint32_t st_h = stage;
-                                if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                    tc_abort<CG>(rc, peer_abort);
-                                    ok = false;
-                                    break;
-                                }
-                                *(volatile unsigned int *)&tl.consumed = ++consumed;
-                                const uint32_t sh = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
-                                if (++stage == C::STAGES) {
-                                    stage = 0;
-                                    phase ^= 1u;
-                                }
-                                const uint32_t st_l = stage;
-                                if (!mbar_wait(&tl.full[stage], phase, abort, p.timeout_ns, p.err)) {
-                                    tc_abort<CG>(rc, peer_abort);
-                                    ok = false;
-                                    break;
-                                }
-                                *(volatile unsigned int *)&tl.consumed = ++consumed;
-                                const uint32_t sl = smem_u32(stages + (size_t)stage * C::STAGE_BYTES);
-                                if (++stage == C::STAGES) {
-                                    stage = 0;
-                                    phase ^= 1u;
-                                }
-                                tc_fence_after();
-#pragma unroll
-                                for (int k = 0; k < TC_BK / 16; ++k)   // A hi x B lo
-                                    umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32),
-                                                 sdesc_sw128(sl + C::A_BYTES + k * 32), idesc,
-                                                 (kb | pr | k) != 0 ? 1u : 0u);
-#pragma unroll
-                                for (int k = 0; k < TC_BK / 16; ++k)   // A lo x B hi
-                                    umma_f16<CG>(d_tmem, sdesc_sw128(sl + k * 32),
-                                                 sdesc_sw128(sh + C::A_BYTES + k * 32), idesc, 1u);
-#pragma unroll
-                                for (int k = 0; k < TC_BK / 16; ++k)   // A hi x B hi
-                                    umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32),
-                                                 sdesc_sw128(sh + C::A_BYTES + k * 32), idesc, 1u);
-                                umma_commit<CG>(&tl.empty[st_h]);
-                                umma_commit<CG>(&tl.empty[st_l]);
-                            }
-                        }
-                    }
-                    umma_commit<CG>(&tl.tfull[acc]);
-                    if (++acc == 2) {
-                        acc = 0;
-                        acc_phase ^= 1u;
-                    }
-                    if (!ok) break;
+                    for (int k = 0; k < TC_BK / 16; ++k)   // A hi x B hi
+                        umma_f16<CG>(d_tmem, sdesc_sw128(sh + k * 32),
+                                     sdesc_sw128(sh + C::A_BYTES + k * 32), idesc, 1u);
+                    umma_commit<CG>(&tl.empty[st_h]);
+                    umma_commit<CG>(&tl.empty[st_l]);
                 }
+            }
+        }
+        umma_commit<CG>(&tl.tfull[acc]);
+        if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1u;
+        }
+        return ok;
+    };
+    const int ew = warp - 2;                  // epilogue warp 0 .. EPI_WARPS - 1
+    const int quarter = warp & 3;             // TMEM lanes this warp may access
+    const int half = ew >> 2;                 // column half of the tile this warp owns
+    uint32_t *T = (uint32_t *)(epi_T + (warp >= 2 ? ew : 0) * EPI_T_FLOATS);   // packed split operands
+    bool flow_first = true;                   // dataflow: no tile completed by this CTA yet
+    // Epilogue: the next layer from tile w's accumulator, its FP64 partials and, in
+    // the dataflow schedule, the tile's completion flag.
+    auto epilogue_tile = [&](const TileWork &w) {
+        const InstDesc &d = p.inst[w.inst];
+        const int np = d.np;
+        const size_t mat = (size_t)np * np;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(&tl.tfull[acc], acc_phase, abort, p.timeout_ns, p.err) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        tc_fence_after();
+        const float *__restrict__ old;
+        float *__restrict__ outf;
+        uint16_t *__restrict__ o1;   // hi
+        uint16_t *__restrict__ o2;   // lo
+        if (!w.resp) {
+            old = xmaster(d, w.n, w.rec != 0);
+            outf = xmaster(d, w.n + 1, w.rec != 0);
+            o1 = d.xop + (size_t)xslot_of(d, w.n + 1) * 2 * mat;
+            o2 = o1 + mat;
+        } else {
+            const int yout = w.ybuf ^ 1;
+            old = d.yf[w.ybuf];
+            outf = d.yf[yout];
+            o1 = d.yop + (size_t)yout * 2 * mat;
+            o2 = o1 + mat;
+        }
+        const float unscale = product_unscale<PREC>(w.resp != 0);
+        const int rw0 = w.bi * C::TILE_M + (int)rank * 128 + quarter * 32;  // first row of this warp
+        const int r = rw0 + lane;
+        const int nreal = d.n;
+        const float cf = w.cf;
+        // Accelerated layer (a != 1) in terms of the product P of the stored
+        // centred operands Y = X - I/2 (true Y = Y + cI): with T = aY + (1 - a/2) I
+        // (X^2 branch) or T = aY + (a/2) I (2X - X^2 branch),
+        //   X_{n+1} = ka (P + 2cY) + kb (Y + cI) + kc I,
+        // ka = +-a^2, kb = a (2 - a), kc = (1 - a/2)^2 or a (1 - a/4); the
+        // response / adjoint stream takes ka P + (kb + 2c ka) X1.
+        const bool accel = (w.alpha != 1.0f);
+        const float al = w.alpha;
+        const float ka = w.flip ? -al * al : al * al;
+        const float kb = al * (2.0f - al);
+        const float kc = w.flip ? al * (1.0f - 0.25f * al) : (1.0f - 0.5f * al) * (1.0f - 0.5f * al);
+        const float kx1 = fmaf(2.0f * cf, ka, kb);
+        // ||Y||_F^2 of the next operands equals ||X||_F^2 off the diagonal (y = x
+        // there); the diagonal difference y^2 - x^2 is added in FP64 (exact squares).
+        FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fp = {0.f, 0.f};
+        double dw = 0.0;
+        if (ok && rw0 < np) {
+#pragma unroll 1
+            // The chunks this warp finishes form one range [j0, j1): chunks entirely
+            // below the diagonal come first, chunks past np last.
+            int j0 = 0, j1 = 128 / EPI_CHUNK;
+            while (j1 > 0 && w.bj * TC_BN + half * 128 + (j1 - 1) * EPI_CHUNK >= np) --j1;
+            while (j0 < j1 && w.bj * TC_BN + half * 128 + j0 * EPI_CHUNK + EPI_CHUNK - 1 < rw0) ++j0;
+            // The previous layer's (r, c) values -- (c, r) by symmetry, coalesced across
+            // the warp, evict-first -- are loaded one chunk ahead, so that their latency
+            // overlaps the current chunk's arithmetic and stores.
+            float xnx[EPI_CHUNK];
+            if (j0 < j1) {
+                const int cb0 = w.bj * TC_BN + half * 128 + j0 * EPI_CHUNK;
+#pragma unroll
+                for (int jj = 0; jj < EPI_CHUNK; ++jj) xnx[jj] = __ldcs(old + (size_t)(cb0 + jj) * np + r);
+            }
+#pragma unroll 1
+            for (int j = j0; j < j1; ++j) {
+                const int c0 = half * 128 + j * EPI_CHUNK;   // column offset in the tile
+                const int cb = w.bj * TC_BN + c0;
+                float xov[EPI_CHUNK];
+#pragma unroll
+                for (int jj = 0; jj < EPI_CHUNK; ++jj) xov[jj] = xnx[jj];
+                if (j + 1 < j1) {
+#pragma unroll
+                    for (int jj = 0; jj < EPI_CHUNK; ++jj)
+                        xnx[jj] = __ldcs(old + (size_t)(cb + EPI_CHUNK + jj) * np + r);
+                }
+                float v[EPI_CHUNK];
+                tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + c0, v);
+                // Each element's next split operands are computed once, stored to the
+                // mirror (c, r) and staged packed (hi | lo << 16) for the direct (r, c)
+                // stores below.  The FP32 master gets the mirror and the diagonal only.
+                const bool upper = (cb > rw0 + 31);     // every element has r < c
+                if (upper && !w.resp && !accel) {
+                    // The common case: a plain square-chain layer, strictly upper chunk.
+                    const float twoc = 2.0f * cf;
+#pragma unroll
+                    for (int jj = 0; jj < EPI_CHUNK; ++jj) {
+                        const int c = cb + jj;
+                        const float xo = xov[jj];
+                        const float t = fmaf(twoc, xo, v[jj] * unscale);
+                        const float x = w.flip ? xo - t : t + xo;   // 2X - X^2 or X^2
+                        ff_add_sq(fq, x, 2.0f);
+                        const size_t m = (size_t)c * np + r;
+                        __stcs(outf + m, x);
+                        uint16_t a1, a2;
+                        split2<PREC, X_SHIFT>(x, a1, a2);
+                        __stcs(o1 + m, a1);
+                        __stcs(o2 + m, a2);
+                        T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
+                    }
+                } else if (upper && w.resp && !accel) {
+                    // Response / adjoint stream, plain layer, strictly upper chunk:
+                    // X X1 + X1 X = P + (1 + 2c) X1, negated for 2X - X^2 (as below).
+                    const float kx = w.flip ? 1.0f - 2.0f * cf : 1.0f + 2.0f * cf;
+                    const float sg = w.flip ? -unscale : unscale;
+#pragma unroll
+                    for (int jj = 0; jj < EPI_CHUNK; ++jj) {
+                        const int c = cb + jj;
+                        const float x = fmaf(kx, xov[jj], v[jj] * sg);
+                        const size_t m = (size_t)c * np + r;
+                        __stcs(outf + m, x);
+                        uint16_t a1, a2;
+                        split2<PREC, Y_SHIFT>(x, a1, a2);
+                        __stcs(o1 + m, a1);
+                        __stcs(o2 + m, a2);
+                        T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < EPI_CHUNK; ++jj) {
+                        const int c = cb + jj;
+                        const float P = v[jj] * unscale;            // raw product
+                        const float xo = xov[jj];
+                        const bool dg = (r == c) && (r < nreal);
+                        float x;
+                        if (!w.resp) {
+                            // P = Y^2 for the stored operands Y = X - I/2; the true input is
+                            // X + cI, so X^2 = P + 2cY + cI + X - I/4 (c^2 is below FP32 here).
+                            const float yo = dg ? xo - 0.5f : xo;
+                            if (accel) {
+                                x = fmaf(ka, fmaf(2.0f * cf, yo, P), fmaf(kb, dg ? yo + cf : yo, dg ? kc : 0.0f));
+                            } else {
+                                const float b = dg ? P - 0.25f : P;
+                                if (!w.flip) x = (b + fmaf(2.0f * cf, yo, dg ? cf : 0.0f)) + xo;  // X^2
+                                else x = xo - (b + fmaf(2.0f * cf, yo, dg ? -cf : 0.0f));        // 2X - X^2
+                            }
+                        } else if (accel) {
+                            x = fmaf(kx1, xo, ka * P);
+                        } else {
+                            // P = Y X1 + X1 Y; with X = Y + (1/2 + c) I the chain needs
+                            // X X1 + X1 X = P + (1 + 2c) X1.
+                            x = w.flip ? fmaf(1.0f - 2.0f * cf, xo, -P) : fmaf(1.0f + 2.0f * cf, xo, P);
+                        }
+                        const float y = (dg && !w.resp) ? x - 0.5f : x;  // next operands
+                        uint16_t a1, a2;
+                        if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
+                        else split2<PREC, Y_SHIFT>(y, a1, a2);
+                        if (r <= c) {
+                            if (!w.resp) {
+                                ff_add_sq(fq, x, (r == c) ? 1.0f : 2.0f);
+                                if (r == c) ff_add(ft, x);
+                                if (dg) {
+                                    ff_add(fp, P);
+                                    dw += (double)y * (double)y - (double)x * (double)x;
+                                }
+                            }
+                            // mirror (c, r), consecutive r across the warp; the diagonal
+                            // element's FP32 master value here too
+                            const size_t m = (size_t)c * np + r;
+                            __stcs(outf + m, x);   // streaming stores: keep L2 for the operands
+                            if (r < c) {
+                                __stcs(o1 + m, a1);
+                                __stcs(o2 + m, a2);
+                            }
+                        }
+                        T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
+                    }
+                }
+                __syncwarp();
+                // direct (r, c) split-operand stores through the transpose buffer, two
+                // rows per step: lanes 0..15 row ii, lanes 16..31 row ii + 1 (the
+                // operands need both triangles: TMA loads rows)
+                const int hl = lane >> 4, cl = lane & 15;
+#pragma unroll 4
+                for (int it = 0; it < 16; ++it) {
+                    const int ii = 2 * it + hl;
+                    const int rr = rw0 + ii, cc = cb + cl;
+                    if (upper || rr <= cc) {
+                        const uint32_t pk = T[ii * (EPI_CHUNK + 1) + cl];
+                        const size_t m = (size_t)rr * np + cc;
+                        __stcs(o1 + m, (uint16_t)(pk & 0xFFFFu));
+                        __stcs(o2 + m, (uint16_t)(pk >> 16));
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // Release the accumulator: every lane's loads have completed
+        // (tcgen05.wait::ld); one arrival per warp on the MMA side's barrier.
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+            if (CG == 2) mbar_arrive_cluster(lead_tempty0 + acc * 8u);
+            else mbar_arrive(&tl.tempty[acc]);
+        }
+        if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1u;
+        }
+        if (!w.resp) {
+            const double q = ff_value(fq);
+            double red4[4] = {ff_value(ft), q, q + dw, ff_value(fp)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                for (int o = 16; o > 0; o >>= 1) red4[k] += __shfl_down_sync(0xffffffffu, red4[k], o);
+            if (lane == 0)
+                for (int k = 0; k < 4; ++k) tl.red[ew][k] = red4[k];
+            if (p.dataflow) {
+                // This warp's stores (generic proxy) reach the TMA reads (async
+                // proxy) of any CTA that sees the tile's completion flag (the
+                // flag's writer fences for the CTA after the barrier below).
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
+            if (ew == 0 && lane == 0) {
+                Part s4;
+                s4.t = s4.q = s4.w = s4.p = 0.0;
+                for (int k = 0; k < EPI_WARPS; ++k) {
+                    s4.t += tl.red[k][0];
+                    s4.q += tl.red[k][1];
+                    s4.w += tl.red[k][2];
+                    s4.p += tl.red[k][3];
+                }
+                d.part[(w.n + 1) % 3][w.tile * CG + (int)rank] = s4;
+                if (p.dataflow) {
+                    __threadfence();
+                    // test_hook: CTA 0 withholds its first completion (a CTA that never
+                    // finishes; the other CTAs' waits must run out).
+                    if (!(p.test_hook == 1 && blockIdx.x == 0 && w.n == 0 && flow_first)) {
+                        atomicAdd(p.tile_done + w.tile, 1u);
+                        atomicAdd(p.layer_done, 1u);
+                    }
+                    flow_first = false;
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
+        }
+    };
+
+    if (p.dataflow) {
+        // ------------- dataflow schedule (one instance, density mode) -------------
+        // No grid barrier between layers.  The producer and the MMA thread run on into
+        // the next layer as soon as their own tiles are done (the producer waits per
+        // K block for the tiles that wrote it); only the epilogue needs the layer's
+        // sign and offset, so the epilogue warps alone wait for every tile of the
+        // previous layer, reduce its partials and take the decision.  When the stop
+        // rule fires they halt the CTA: loads and MMAs issued ahead are drained at
+        // teardown.  Each tile's arithmetic, and so X and D, is that of the barrier
+        // schedule bit for bit.
+        const int ntl = p.inst[0].ntiles;
+        if (cluster_id >= ntl) {
+            // no tiles here: only the epilogue warps take part (in the decisions)
+        } else if (warp == 0) {
+            if (lane == 0)
+                for (int r = 0; !*abort; ++r)
+                    for (int g = cluster_id; g < ntl && !*abort; g += nclusters) produce_tile(describe_flow(p, g, r));
+        } else if (warp == 1) {
+            if (lane == 0 && leader) {
+                bool ok = true;
+                for (int r = 0; ok && !*abort; ++r)
+                    for (int g = cluster_id; ok && g < ntl && !*abort; g += nclusters) ok = mma_tile(describe_flow(p, g, r));
             }
         } else {
-            // --------------------------- epilogue ---------------------------
-            const int ew = warp - 2;                  // 0 .. EPI_WARPS - 1
-            const int quarter = warp & 3;             // TMEM lanes this warp may access
-            const int half = ew >> 2;                 // column half of the tile this warp owns
-            uint32_t *T = (uint32_t *)(epi_T + ew * EPI_T_FLOATS);   // packed split operands
-            for (int g = cluster_id; g < rc.total; g += nclusters) {
-                const TileWork w = describe(rc, p, g);
-                const InstDesc &d = p.inst[w.inst];
-                const int np = d.np;
-                const size_t mat = (size_t)np * np;
-                int ok = 1;
-                if (lane == 0) ok = mbar_wait(&tl.tfull[acc], acc_phase, abort, p.timeout_ns, p.err) ? 1 : 0;
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                tc_fence_after();
-                const float *__restrict__ old;
-                float *__restrict__ outf;
-                uint16_t *__restrict__ o1;   // hi
-                uint16_t *__restrict__ o2;   // lo
-                if (!w.resp) {
-                    old = xmaster(d, w.n, w.rec != 0);
-                    outf = xmaster(d, w.n + 1, w.rec != 0);
-                    o1 = d.xop + (size_t)xslot_of(d, w.n + 1) * 2 * mat;
-                    o2 = o1 + mat;
-                } else {
-                    const int yout = w.ybuf ^ 1;
-                    old = d.yf[w.ybuf];
-                    outf = d.yf[yout];
-                    o1 = d.yop + (size_t)yout * 2 * mat;
-                    o2 = o1 + mat;
+            for (int r = 0;; ++r) {
+                if (!flow_decide(rc, p, tl.red[0], r, ew, lane, ntl * CG, abort)) {
+                    tc_abort<CG>(rc, peer_abort);   // stop rule or error: halt this CTA and its peer
+                    break;
                 }
-                const float unscale = product_unscale<PREC>(w.resp != 0);
-                const int rw0 = w.bi * C::TILE_M + (int)rank * 128 + quarter * 32;  // first row of this warp
-                const int r = rw0 + lane;
-                const int nreal = d.n;
-                const float cf = w.cf;
-                // Accelerated layer (a != 1) in terms of the product P of the stored
-                // centred operands Y = X - I/2 (true Y = Y + cI): with T = aY + (1 - a/2) I
-                // (X^2 branch) or T = aY + (a/2) I (2X - X^2 branch),
-                //   X_{n+1} = ka (P + 2cY) + kb (Y + cI) + kc I,
-                // ka = +-a^2, kb = a (2 - a), kc = (1 - a/2)^2 or a (1 - a/4); the
-                // response / adjoint stream takes ka P + (kb + 2c ka) X1.
-                const bool accel = (w.alpha != 1.0f);
-                const float al = w.alpha;
-                const float ka = w.flip ? -al * al : al * al;
-                const float kb = al * (2.0f - al);
-                const float kc = w.flip ? al * (1.0f - 0.25f * al) : (1.0f - 0.5f * al) * (1.0f - 0.5f * al);
-                const float kx1 = fmaf(2.0f * cf, ka, kb);
-                // ||Y||_F^2 of the next operands equals ||X||_F^2 off the diagonal (y = x
-                // there); the diagonal difference y^2 - x^2 is added in FP64 (exact squares).
-                FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fp = {0.f, 0.f};
-                double dw = 0.0;
-                if (ok && rw0 < np) {
-#pragma unroll 1
-                    // The chunks this warp finishes form one range [j0, j1): chunks entirely
-                    // below the diagonal come first, chunks past np last.
-                    int j0 = 0, j1 = 128 / EPI_CHUNK;
-                    while (j1 > 0 && w.bj * TC_BN + half * 128 + (j1 - 1) * EPI_CHUNK >= np) --j1;
-                    while (j0 < j1 && w.bj * TC_BN + half * 128 + j0 * EPI_CHUNK + EPI_CHUNK - 1 < rw0) ++j0;
-                    // The previous layer's (r, c) values -- (c, r) by symmetry, coalesced across
-                    // the warp, evict-first -- are loaded one chunk ahead, so that their latency
-                    // overlaps the current chunk's arithmetic and stores.
-                    float xnx[EPI_CHUNK];
-                    if (j0 < j1) {
-                        const int cb0 = w.bj * TC_BN + half * 128 + j0 * EPI_CHUNK;
-#pragma unroll
-                        for (int jj = 0; jj < EPI_CHUNK; ++jj) xnx[jj] = __ldcs(old + (size_t)(cb0 + jj) * np + r);
-                    }
-#pragma unroll 1
-                    for (int j = j0; j < j1; ++j) {
-                        const int c0 = half * 128 + j * EPI_CHUNK;   // column offset in the tile
-                        const int cb = w.bj * TC_BN + c0;
-                        float xov[EPI_CHUNK];
-#pragma unroll
-                        for (int jj = 0; jj < EPI_CHUNK; ++jj) xov[jj] = xnx[jj];
-                        if (j + 1 < j1) {
-#pragma unroll
-                            for (int jj = 0; jj < EPI_CHUNK; ++jj)
-                                xnx[jj] = __ldcs(old + (size_t)(cb + EPI_CHUNK + jj) * np + r);
-                        }
-                        float v[EPI_CHUNK];
-                        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * TC_BN + c0, v);
-                        // Each element's next split operands are computed once, stored to the
-                        // mirror (c, r) and staged packed (hi | lo << 16) for the direct (r, c)
-                        // stores below.  The FP32 master gets the mirror and the diagonal only.
-                        const bool upper = (cb > rw0 + 31);     // every element has r < c
-                        if (upper && !w.resp && !accel) {
-                            // The common case: a plain square-chain layer, strictly upper chunk.
-                            const float twoc = 2.0f * cf;
-#pragma unroll
-                            for (int jj = 0; jj < EPI_CHUNK; ++jj) {
-                                const int c = cb + jj;
-                                const float xo = xov[jj];
-                                const float t = fmaf(twoc, xo, v[jj] * unscale);
-                                const float x = w.flip ? xo - t : t + xo;   // 2X - X^2 or X^2
-                                ff_add_sq(fq, x, 2.0f);
-                                const size_t m = (size_t)c * np + r;
-                                __stcs(outf + m, x);
-                                uint16_t a1, a2;
-                                split2<PREC, X_SHIFT>(x, a1, a2);
-                                __stcs(o1 + m, a1);
-                                __stcs(o2 + m, a2);
-                                T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
-                            }
-                        } else if (upper && w.resp && !accel) {
-                            // Response / adjoint stream, plain layer, strictly upper chunk:
-                            // X X1 + X1 X = P + (1 + 2c) X1, negated for 2X - X^2 (as below).
-                            const float kx = w.flip ? 1.0f - 2.0f * cf : 1.0f + 2.0f * cf;
-                            const float sg = w.flip ? -unscale : unscale;
-#pragma unroll
-                            for (int jj = 0; jj < EPI_CHUNK; ++jj) {
-                                const int c = cb + jj;
-                                const float x = fmaf(kx, xov[jj], v[jj] * sg);
-                                const size_t m = (size_t)c * np + r;
-                                __stcs(outf + m, x);
-                                uint16_t a1, a2;
-                                split2<PREC, Y_SHIFT>(x, a1, a2);
-                                __stcs(o1 + m, a1);
-                                __stcs(o2 + m, a2);
-                                T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
-                            }
-                        } else {
-#pragma unroll
-                            for (int jj = 0; jj < EPI_CHUNK; ++jj) {
-                                const int c = cb + jj;
-                                const float P = v[jj] * unscale;            // raw product
-                                const float xo = xov[jj];
-                                const bool dg = (r == c) && (r < nreal);
-                                float x;
-                                if (!w.resp) {
-                                    // P = Y^2 for the stored operands Y = X - I/2; the true input is
-                                    // X + cI, so X^2 = P + 2cY + cI + X - I/4 (c^2 is below FP32 here).
-                                    const float yo = dg ? xo - 0.5f : xo;
-                                    if (accel) {
-                                        x = fmaf(ka, fmaf(2.0f * cf, yo, P), fmaf(kb, dg ? yo + cf : yo, dg ? kc : 0.0f));
-                                    } else {
-                                        const float b = dg ? P - 0.25f : P;
-                                        if (!w.flip) x = (b + fmaf(2.0f * cf, yo, dg ? cf : 0.0f)) + xo;  // X^2
-                                        else x = xo - (b + fmaf(2.0f * cf, yo, dg ? -cf : 0.0f));        // 2X - X^2
-                                    }
-                                } else if (accel) {
-                                    x = fmaf(kx1, xo, ka * P);
-                                } else {
-                                    // P = Y X1 + X1 Y; with X = Y + (1/2 + c) I the chain needs
-                                    // X X1 + X1 X = P + (1 + 2c) X1.
-                                    x = w.flip ? fmaf(1.0f - 2.0f * cf, xo, -P) : fmaf(1.0f + 2.0f * cf, xo, P);
-                                }
-                                const float y = (dg && !w.resp) ? x - 0.5f : x;  // next operands
-                                uint16_t a1, a2;
-                                if (!w.resp) split2<PREC, X_SHIFT>(y, a1, a2);
-                                else split2<PREC, Y_SHIFT>(y, a1, a2);
-                                if (r <= c) {
-                                    if (!w.resp) {
-                                        ff_add_sq(fq, x, (r == c) ? 1.0f : 2.0f);
-                                        if (r == c) ff_add(ft, x);
-                                        if (dg) {
-                                            ff_add(fp, P);
-                                            dw += (double)y * (double)y - (double)x * (double)x;
-                                        }
-                                    }
-                                    // mirror (c, r), consecutive r across the warp; the diagonal
-                                    // element's FP32 master value here too
-                                    const size_t m = (size_t)c * np + r;
-                                    __stcs(outf + m, x);   // streaming stores: keep L2 for the operands
-                                    if (r < c) {
-                                        __stcs(o1 + m, a1);
-                                        __stcs(o2 + m, a2);
-                                    }
-                                }
-                                T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
-                            }
-                        }
-                        __syncwarp();
-                        // direct (r, c) split-operand stores through the transpose buffer, two
-                        // rows per step: lanes 0..15 row ii, lanes 16..31 row ii + 1 (the
-                        // operands need both triangles: TMA loads rows)
-                        const int hl = lane >> 4, cl = lane & 15;
-#pragma unroll 4
-                        for (int it = 0; it < 16; ++it) {
-                            const int ii = 2 * it + hl;
-                            const int rr = rw0 + ii, cc = cb + cl;
-                            if (upper || rr <= cc) {
-                                const uint32_t pk = T[ii * (EPI_CHUNK + 1) + cl];
-                                const size_t m = (size_t)rr * np + cc;
-                                __stcs(o1 + m, (uint16_t)(pk & 0xFFFFu));
-                                __stcs(o2 + m, (uint16_t)(pk >> 16));
-                            }
-                        }
-                        __syncwarp();
-                    }
-                }
-                // Release the accumulator: every lane's loads have completed
-                // (tcgen05.wait::ld); one arrival per warp on the MMA side's barrier.
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    if (CG == 2) mbar_arrive_cluster(lead_tempty0 + acc * 8u);
-                    else mbar_arrive(&tl.tempty[acc]);
-                }
-                if (++acc == 2) {
-                    acc = 0;
-                    acc_phase ^= 1u;
-                }
-                if (!w.resp) {
-                    const double q = ff_value(fq);
-                    double red4[4] = {ff_value(ft), q, q + dw, ff_value(fp)};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        for (int o = 16; o > 0; o >>= 1) red4[k] += __shfl_down_sync(0xffffffffu, red4[k], o);
-                    if (lane == 0)
-                        for (int k = 0; k < 4; ++k) tl.red[ew][k] = red4[k];
-                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
-                    if (ew == 0 && lane == 0) {
-                        Part s4;
-                        s4.t = s4.q = s4.w = s4.p = 0.0;
-                        for (int k = 0; k < EPI_WARPS; ++k) {
-                            s4.t += tl.red[k][0];
-                            s4.q += tl.red[k][1];
-                            s4.w += tl.red[k][2];
-                            s4.p += tl.red[k][3];
-                        }
-                        d.part[(w.n + 1) & 1][w.tile * CG + (int)rank] = s4;
-                    }
-                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
-                }
+                for (int g = cluster_id; g < rc.total; g += nclusters) epilogue_tile(describe(rc, p, g));
             }
-            // Order this round's generic-proxy stores before the async-proxy
-            // (TMA) reads of the next round, on any SM.
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            __threadfence();
+        }
+    } else {
+        // --------------- barrier schedule (every other mode and batch) ---------------
+        unsigned int target = 0;
+        bool first = true;
+        while (true) {
+            if (!first) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    const bool withhold = (p.test_hook == 1 && blockIdx.x == 0 && target == 0);
+                    target += gridDim.x;
+                    if (!grid_barrier(p.barrier, target, p.err, p.timeout_ns, withhold)) rc.abort = 1;
+                }
+                __syncthreads();
+                if (rc.abort) break;
+            }
+            first = false;
+            // The epilogue transpose buffers are idle here: use them for the sums.
+            reduce_round_partials(rc, p, (double *)epi_T);
+            if (p.mode == MODE_ADJOINT) {
+                if (threadIdx.x == 0) decide_round(rc, p, (const double *)epi_T);
+            } else {
+                decide_round_parallel(rc, p, (const double *)epi_T, (int *)((double *)epi_T + 4 * MAX_BATCH));
+            }
+            if (threadIdx.x == 0) {
+                // Make the previous round's global writes (other CTAs' epilogues,
+                // generic proxy) visible to this CTA's TMA reads (async proxy).
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            __syncthreads();
+            if (rc.abort || rc.total == 0) break;
+
+            if (warp == 0) {
+                if (lane == 0)
+                    for (int g = cluster_id; g < rc.total && !*abort; g += nclusters) produce_tile(describe(rc, p, g));
+            } else if (warp == 1) {
+                if (lane == 0 && leader)
+                    for (int g = cluster_id; g < rc.total && !*abort; g += nclusters)
+                        if (!mma_tile(describe(rc, p, g))) break;
+            } else {
+                for (int g = cluster_id; g < rc.total; g += nclusters) epilogue_tile(describe(rc, p, g));
+                // Order this round's generic-proxy stores before the async-proxy
+                // (TMA) reads of the next round, on any SM.
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __threadfence();
+            }
         }
     }
 

@@ -309,7 +309,7 @@ def adjoint(H: torch.Tensor, G: torch.Tensor, n_occ: int, tol: float = 1e-6, pre
 def density_batched(Hs: Sequence[torch.Tensor], n_occs: Sequence[int], tol: float = 1e-6,
                     precision: str = "bf16", max_layers: int = 100, timeout_ms: float = 2000.0,
                     outs: Optional[Sequence[torch.Tensor]] = None, workspace: Optional[torch.Tensor] = None,
-                    stream=None):
+                    stream=None, cta_group: int = 0):
     """Independent chains in one grouped launch; returns (list of D, list of Result, worst status)."""
     B = len(Hs)
     Hs = [_f64(h, f"H[{i}]") for i, h in enumerate(Hs)]
@@ -326,7 +326,7 @@ def density_batched(Hs: Sequence[torch.Tensor], n_occs: Sequence[int], tol: floa
     dp = (ctypes.c_void_p * B)(*[d.data_ptr() for d in Ds])
     nn = (ctypes.c_int * B)(*ns)
     occ = (ctypes.c_double * B)(*[float(x) for x in n_occs])
-    o = make_opts(precision, max_layers, timeout_ms)
+    o = make_opts(precision, max_layers, timeout_ms, cta_group=cta_group)
     ws, wsb = _ws_args(workspace)
     s = load().sp2_density_batched(B, hp, nn, occ, float(tol), dp, sts, ctypes.byref(o), ws, wsb,
                                    ctypes.c_void_p(_stream_handle(Hs[0], stream)))

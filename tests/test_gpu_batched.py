@@ -43,3 +43,22 @@ def test_batched_workload_64_instances():
     errs = [fro_err(host(D), odens.density_from_eigensystem(h.eigvecs, h.n_occ)) for h, D in zip(hams, Ds)]
     print(f"\nbatched 64: max err {max(errs):.2e}, layers {min(r.layers for r in res)}..{max(r.layers for r in res)}")
     assert max(errs) <= TOL_D["bf16"]
+
+
+@pytest.mark.parametrize("cta_group", [1, 2])
+def test_dataflow_schedule_equals_barrier_schedule(cta_group):
+    """A lone density solve runs its layers without a grid barrier between them (each
+    K block waits for the tiles that wrote it, the decision waits for the whole layer);
+    the same instance in a batch runs with the barrier.  Every tile's arithmetic is the
+    same, so D and every layer's statistics agree bit for bit, here over several waves
+    of tiles (N = 4096: 136 pair tiles, 272 single-CTA tiles)."""
+    ham = inputs.water_like_workload(4096)
+    H = dev(ham.H)
+    D1, r1 = sp2.density(H, ham.n_occ, precision="fp16", cta_group=cta_group)
+    small = inputs.gapped_random(128, 64, inputs.rng_for(2, 1))
+    Ds, res, status = sp2.density_batched([H, dev(small.H)], [ham.n_occ, 64], precision="fp16",
+                                          cta_group=cta_group)
+    assert status == sp2.OK and r1.converged
+    assert r1.cta_group == cta_group
+    assert torch.equal(Ds[0], D1)
+    assert res[0].choices == r1.choices and res[0].trace == r1.trace and res[0].trace_sq == r1.trace_sq
