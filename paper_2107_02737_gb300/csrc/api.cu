@@ -54,6 +54,29 @@ bool encode_op_map(CUtensorMap *m, const void *base, int np, int precision) {
     return r == CUDA_SUCCESS;
 }
 
+// 2-D map over an np x np 16-bit matrix for the epilogue's stores: box EPI_BOX_COLS
+// x EPI_BOX_ROWS, no swizzle (the box sits row-major in shared memory).
+bool encode_store_map(CUtensorMap *m, const void *base, int np) {
+    EncodeTiledFn fn = get_encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)np};
+    cuuint64_t strides[1] = {(cuuint64_t)np * 2};
+    cuuint32_t box[2] = {(cuuint32_t)EPI_BOX_COLS, (cuuint32_t)EPI_BOX_ROWS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// The MAPS_PER_SLOT maps of one operand slot (matrices hi at `hi`, lo at hi + np^2).
+bool encode_slot_maps(CUtensorMap *m, const uint16_t *hi, int np, int precision) {
+    const size_t mat = (size_t)np * np;
+    for (int k = 0; k < 3; ++k)
+        if (!encode_op_map(&m[k], hi + (k == 2 ? mat : 0), np, precision)) return false;
+    return encode_store_map(&m[3], hi, np) && encode_store_map(&m[4], hi + mat, np);
+}
+
 struct DeviceInfo {
     int sm = 0, major = 0, minor = 0;
     cudaError_t err = cudaSuccess;
@@ -259,7 +282,7 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
         c.take(mat * 4);
         if (pl.path == PATH_TC) {
             c.take((size_t)pl.slots[i] * 2 * mat * 2);
-            c.take((size_t)pl.slots[i] * 3 * sizeof(CUtensorMap));
+            c.take((size_t)pl.slots[i] * MAPS_PER_SLOT * sizeof(CUtensorMap));
             if (pl.ckpt_s[i] > 0) {
                 c.take((size_t)pl.ckpt_k[i] * mat * 4);
                 c.take(mat * 4);
@@ -269,7 +292,7 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
                 c.take(mat * 4);
                 c.take(mat * 4);
                 c.take(2 * 2 * mat * 2);
-                c.take(6 * sizeof(CUtensorMap));
+                c.take(2 * MAPS_PER_SLOT * sizeof(CUtensorMap));
             }
         }
     }
@@ -456,16 +479,15 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         d.xf[1] = (float *)c.take(mat * 4);
         if (pl.path == PATH_TC) {
             d.xop = (uint16_t *)c.take((size_t)d.nslots_x * 2 * mat * 2);
-            d_xmaps[i] = (CUtensorMap *)c.take((size_t)d.nslots_x * 3 * sizeof(CUtensorMap));
+            d_xmaps[i] = (CUtensorMap *)c.take((size_t)d.nslots_x * MAPS_PER_SLOT * sizeof(CUtensorMap));
             d.xmap = d_xmaps[i];
-            h_xmaps[i].resize((size_t)d.nslots_x * 3);
-            // Three maps per slot for the K segments' operands op0, op1, op2 = hi, hi, lo
-            // over the slot's two matrices (hi, lo).
+            h_xmaps[i].resize((size_t)d.nslots_x * MAPS_PER_SLOT);
+            // Per slot: the K segments' operands op0, op1, op2 = hi, hi, lo over the
+            // slot's two matrices (hi, lo), then the epilogue's store maps of hi and lo.
             for (int sl = 0; sl < d.nslots_x; ++sl)
-                for (int k = 0; k < 3; ++k)
-                    if (!encode_op_map(&h_xmaps[i][sl * 3 + k], d.xop + ((size_t)sl * 2 + (k == 2)) * mat, np,
-                                       pl.precision))
-                        return SP2_ERR_UNSUPPORTED;
+                if (!encode_slot_maps(&h_xmaps[i][(size_t)sl * MAPS_PER_SLOT], d.xop + (size_t)sl * 2 * mat, np,
+                                      pl.precision))
+                    return SP2_ERR_UNSUPPORTED;
             if (pl.ckpt_s[i] > 0) {
                 d.ckpt_s = pl.ckpt_s[i];
                 d.ckpt_k = pl.ckpt_k[i];
@@ -477,14 +499,13 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
                 d.yf[0] = (float *)c.take(mat * 4);
                 d.yf[1] = (float *)c.take(mat * 4);
                 d.yop = (uint16_t *)c.take(2 * 2 * mat * 2);
-                d_ymaps[i] = (CUtensorMap *)c.take(6 * sizeof(CUtensorMap));
+                d_ymaps[i] = (CUtensorMap *)c.take(2 * MAPS_PER_SLOT * sizeof(CUtensorMap));
                 d.ymap = d_ymaps[i];
-                h_ymaps[i].resize(6);
+                h_ymaps[i].resize(2 * MAPS_PER_SLOT);
                 for (int sl = 0; sl < 2; ++sl)
-                    for (int k = 0; k < 3; ++k)
-                        if (!encode_op_map(&h_ymaps[i][sl * 3 + k], d.yop + ((size_t)sl * 2 + (k == 2)) * mat, np,
-                                           pl.precision))
-                            return SP2_ERR_UNSUPPORTED;
+                    if (!encode_slot_maps(&h_ymaps[i][(size_t)sl * MAPS_PER_SLOT], d.yop + (size_t)sl * 2 * mat, np,
+                                          pl.precision))
+                        return SP2_ERR_UNSUPPORTED;
             }
         }
         InstCtl &ctl = h_ctl[i];

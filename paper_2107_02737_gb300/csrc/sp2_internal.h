@@ -39,6 +39,9 @@ constexpr int TC_BM = 128;          // tcgen05 tile rows (UMMA M)
 constexpr int TC_BN = 256;          // tcgen05 tile columns (UMMA N)
 constexpr int TC_BK = 64;           // K block: 64 x 16-bit = one 128-byte swizzle row
 constexpr int TC_STAGES = 4;        // TMA -> MMA pipeline depth
+constexpr int MAPS_PER_SLOT = 5;    // per operand slot: loads hi, hi, lo (64 x 128 boxes); stores hi, lo
+constexpr int EPI_BOX_COLS = 16;    // store box: one epilogue warp's chunk of 32 rows x 16 columns
+constexpr int EPI_BOX_ROWS = 32;
 constexpr int TC_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue (two per SM sub-partition)
 constexpr int SIMT_T = 128;         // FP32 SIMT tile (square)
 constexpr int SIMT_THREADS = 256;
@@ -98,8 +101,9 @@ struct InstDesc {
     uint16_t *yop;                    // slot s in {0,1}: hi, lo as for xop
     Part *part[3];                    // by layer n mod 3 (three deep for the dataflow schedule)
     int part_cap, fin_blocks;
-    const CUtensorMap *xmap;          // [nslots_x * 3]: per slot the K segments' op0, op1, op2 = hi, hi, lo
-    const CUtensorMap *ymap;          // [2 * 3]
+    const CUtensorMap *xmap;          // [nslots_x * MAPS_PER_SLOT]: per slot the K segments' loads op0, op1,
+                                      // op2 = hi, hi, lo, then the epilogue's stores of hi and lo
+    const CUtensorMap *ymap;          // [2 * MAPS_PER_SLOT]
     const double *H;                  // device copy of H (n x n)
     const double *H1;                 // response perturbation or adjoint weight (n x n)
     float *out;                       // D (n x n)

@@ -63,7 +63,13 @@ struct Cfg {
 constexpr int MAX_STAGES = 6;
 constexpr int EPI_WARPS = 8;                              // warps 2..9
 constexpr int EPI_CHUNK = 16;                             // accumulator columns per epilogue step
-constexpr uint32_t EPI_T_FLOATS = 32 * (EPI_CHUNK + 1);   // transpose buffer per epilogue warp
+// Per epilogue warp: the transpose buffer of a chunk (32 x (EPI_CHUNK + 1) words) or
+// the chunk's hi and lo boxes for the tensor stores, 128-byte aligned.
+constexpr uint32_t EPI_T_FLOATS = 576;
+static_assert(EPI_CHUNK == EPI_BOX_COLS && EPI_BOX_ROWS == 32, "store box = one warp's chunk");
+static_assert(EPI_T_FLOATS >= 32 * (EPI_CHUNK + 1) && EPI_T_FLOATS * 4 >= 2 * EPI_BOX_ROWS * EPI_BOX_COLS * 2 &&
+                  (EPI_T_FLOATS * 4) % 128 == 0,
+              "epilogue buffer");
 constexpr uint32_t TMEM_COLS = 512;                       // two 128 x 256 FP32 accumulators
 
 struct TcSmemTail {
@@ -264,6 +270,18 @@ __device__ __noinline__ bool flow_decide(RoundCtl &rc, const RunParams &p, doubl
     return rc.total > 0;
 }
 
+// Element jj of a lane's chunk row into the packed column pairs of its hi and lo boxes.
+__device__ __forceinline__ void pack_pair(uint32_t (&hp)[EPI_CHUNK / 2], uint32_t (&lp)[EPI_CHUNK / 2], int jj,
+                                          uint16_t a1, uint16_t a2) {
+    if (jj & 1) {
+        hp[jj >> 1] |= (uint32_t)a1 << 16;
+        lp[jj >> 1] |= (uint32_t)a2 << 16;
+    } else {
+        hp[jj >> 1] = a1;
+        lp[jj >> 1] = a2;
+    }
+}
+
 template <int PREC, int CG>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_constant__ RunParams p) {
     using C = Cfg<CG>;
@@ -377,7 +395,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         // (lo, lo), which feed all three products.  Response tiles: the six
         // segments one after another, one K block per slot.
         const int nslot = (w.resp ? 4 : 2) * nkb;
-        const CUtensorMap *X3 = d.xmap + w.xslot * 3;   // maps hi, hi, lo
+        const CUtensorMap *X3 = d.xmap + w.xslot * MAPS_PER_SLOT;   // maps hi, hi, lo
         for (int kb = 0; kb < nslot; ++kb) {
             int kx;
             const CUtensorMap *am, *bm;
@@ -385,7 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 // Response / adjoint tiles: per K block (X hi, Y hi), (X lo, Y lo),
                 // (Y hi, X hi), (Y lo, X lo) -- rows bi on the A side, rows bj on the B
                 // side -- feeding X Y^T and Y X^T.
-                const CUtensorMap *Y3 = d.ymap + w.ybuf * 3;
+                const CUtensorMap *Y3 = d.ymap + w.ybuf * MAPS_PER_SLOT;
                 const int q = kb & 3;
                 kx = (kdown ? nkb - 1 - (kb >> 2) : (kb >> 2)) * TC_BK;
                 const CUtensorMap *xm = (q & 1) ? X3 + 2 : X3 + 1, *ym = (q & 1) ? Y3 + 2 : Y3 + 1;
@@ -556,6 +574,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     const int quarter = warp & 3;             // TMEM lanes this warp may access
     const int half = ew >> 2;                 // column half of the tile this warp owns
     uint32_t *T = (uint32_t *)(epi_T + (warp >= 2 ? ew : 0) * EPI_T_FLOATS);   // packed split operands
+    uint16_t *Bh = (uint16_t *)T, *Bl = Bh + EPI_BOX_ROWS * EPI_BOX_COLS;      // or the hi and lo boxes
     bool flow_first = true;                   // dataflow: no tile completed by this CTA yet
     // Epilogue: the next layer from tile w's accumulator, its FP64 partials and, in
     // the dataflow schedule, the tile's completion flag.
@@ -571,17 +590,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         float *__restrict__ outf;
         uint16_t *__restrict__ o1;   // hi
         uint16_t *__restrict__ o2;   // lo
+        const CUtensorMap *smap;     // store maps of hi, lo
         if (!w.resp) {
             old = xmaster(d, w.n, w.rec != 0);
             outf = xmaster(d, w.n + 1, w.rec != 0);
-            o1 = d.xop + (size_t)xslot_of(d, w.n + 1) * 2 * mat;
+            const int so = xslot_of(d, w.n + 1);
+            o1 = d.xop + (size_t)so * 2 * mat;
             o2 = o1 + mat;
+            smap = d.xmap + (size_t)so * MAPS_PER_SLOT + 3;
         } else {
             const int yout = w.ybuf ^ 1;
             old = d.yf[w.ybuf];
             outf = d.yf[yout];
             o1 = d.yop + (size_t)yout * 2 * mat;
             o2 = o1 + mat;
+            smap = d.ymap + (size_t)yout * MAPS_PER_SLOT + 3;
         }
         const float unscale = product_unscale<PREC>(w.resp != 0);
         const int rw0 = w.bi * C::TILE_M + (int)rank * 128 + quarter * 32;  // first row of this warp
@@ -605,7 +628,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fp = {0.f, 0.f};
         double dw = 0.0;
         if (ok && rw0 < np) {
-#pragma unroll 1
             // The chunks this warp finishes form one range [j0, j1): chunks entirely
             // below the diagonal come first, chunks past np last.
             int j0 = 0, j1 = 128 / EPI_CHUNK;
@@ -638,6 +660,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                 // mirror (c, r) and staged packed (hi | lo << 16) for the direct (r, c)
                 // stores below.  The FP32 master gets the mirror and the diagonal only.
                 const bool upper = (cb > rw0 + 31);     // every element has r < c
+                // Strictly upper chunks of plain layers write their direct (r, c) operands
+                // as two boxes of tensor stores; the others through the transpose buffer,
+                // once the previous chunk's boxes have left it.
+                const bool boxed = upper && !accel;
+                if (!boxed) {
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
+                }
+                uint32_t hp[EPI_CHUNK / 2], lp[EPI_CHUNK / 2];   // (r, c), (r, c + 1) packed
                 if (upper && !w.resp && !accel) {
                     // The common case: a plain square-chain layer, strictly upper chunk.
                     const float twoc = 2.0f * cf;
@@ -654,7 +685,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                         split2<PREC, X_SHIFT>(x, a1, a2);
                         __stcs(o1 + m, a1);
                         __stcs(o2 + m, a2);
-                        T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
+                        pack_pair(hp, lp, jj, a1, a2);
                     }
                 } else if (upper && w.resp && !accel) {
                     // Response / adjoint stream, plain layer, strictly upper chunk:
@@ -671,7 +702,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                         split2<PREC, Y_SHIFT>(x, a1, a2);
                         __stcs(o1 + m, a1);
                         __stcs(o2 + m, a2);
-                        T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
+                        pack_pair(hp, lp, jj, a1, a2);
                     }
                 } else {
 #pragma unroll
@@ -724,23 +755,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                         T[lane * (EPI_CHUNK + 1) + jj] = (uint32_t)a1 | ((uint32_t)a2 << 16);
                     }
                 }
-                __syncwarp();
-                // direct (r, c) split-operand stores through the transpose buffer, two
-                // rows per step: lanes 0..15 row ii, lanes 16..31 row ii + 1 (the
-                // operands need both triangles: TMA loads rows)
-                const int hl = lane >> 4, cl = lane & 15;
-#pragma unroll 4
-                for (int it = 0; it < 16; ++it) {
-                    const int ii = 2 * it + hl;
-                    const int rr = rw0 + ii, cc = cb + cl;
-                    if (upper || rr <= cc) {
-                        const uint32_t pk = T[ii * (EPI_CHUNK + 1) + cl];
-                        const size_t m = (size_t)rr * np + cc;
-                        __stcs(o1 + m, (uint16_t)(pk & 0xFFFFu));
-                        __stcs(o2 + m, (uint16_t)(pk >> 16));
+                if (boxed) {
+                    // The chunk's 32 x 16 boxes of hi and lo, row-major, to global memory
+                    // by the tensor store unit (the operands need both triangles: TMA
+                    // loads rows).
+                    if (lane == 0) bulk_wait_read();   // the previous boxes have left the buffer
+                    __syncwarp();
+                    uint4 *bh = (uint4 *)(Bh + lane * EPI_BOX_COLS), *bl = (uint4 *)(Bl + lane * EPI_BOX_COLS);
+                    bh[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+                    bh[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+                    bl[0] = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+                    bl[1] = make_uint4(lp[4], lp[5], lp[6], lp[7]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(smap, Bh, cb, rw0);
+                        tma_store_2d(smap + 1, Bl, cb, rw0);
+                        bulk_commit();
                     }
+                } else {
+                    __syncwarp();
+                    // direct (r, c) split-operand stores through the transpose buffer, two
+                    // rows per step: lanes 0..15 row ii, lanes 16..31 row ii + 1
+                    const int hl = lane >> 4, cl = lane & 15;
+#pragma unroll 4
+                    for (int it = 0; it < 16; ++it) {
+                        const int ii = 2 * it + hl;
+                        const int rr = rw0 + ii, cc = cb + cl;
+                        if (upper || rr <= cc) {
+                            const uint32_t pk = T[ii * (EPI_CHUNK + 1) + cl];
+                            const size_t m = (size_t)rr * np + cc;
+                            __stcs(o1 + m, (uint16_t)(pk & 0xFFFFu));
+                            __stcs(o2 + m, (uint16_t)(pk >> 16));
+                        }
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
         }
         // Release the accumulator: every lane's loads have completed
@@ -764,9 +814,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             if (lane == 0)
                 for (int k = 0; k < 4; ++k) tl.red[ew][k] = red4[k];
             if (p.dataflow) {
-                // This warp's stores (generic proxy) reach the TMA reads (async
-                // proxy) of any CTA that sees the tile's completion flag (the
-                // flag's writer fences for the CTA after the barrier below).
+                // This warp's stores (generic proxy, and its tensor stores once
+                // complete) reach the TMA reads (async proxy) of any CTA that sees the
+                // tile's completion flag (the flag's writer fences for the CTA after
+                // the barrier below).
+                if (lane == 0) {
+                    bulk_wait_all();
+                    __threadfence();
+                }
                 asm volatile("fence.proxy.async.global;" ::: "memory");
             }
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
@@ -867,8 +922,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                         if (!mma_tile(describe(rc, p, g))) break;
             } else {
                 for (int g = cluster_id; g < rc.total; g += nclusters) epilogue_tile(describe(rc, p, g));
-                // Order this round's generic-proxy stores before the async-proxy
-                // (TMA) reads of the next round, on any SM.
+                // This warp's tensor stores are complete; order this round's
+                // generic-proxy stores before the async-proxy (TMA) reads of the next
+                // round, on any SM.
+                if (lane == 0) bulk_wait_all();
+                __syncwarp();
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __threadfence();
             }
@@ -876,6 +934,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
     }
 
     // ------------------------------ teardown ------------------------------
+    // Tensor stores still reading this CTA's shared memory finish before it is released.
+    if (warp >= 2 && lane == 0) bulk_wait_all();
     // After an abort: MMAs this launch issued complete before tensor memory and the
     // stages are released (the commit covers every earlier MMA of the issuing thread).
     if (warp == 1 && lane == 0 && leader && rc.abort) {
