@@ -40,6 +40,26 @@ __device__ __forceinline__ void ff_add_sq(FF &a, float x, float w) {
     a.c = __fadd_rn(a.c, __fmul_rn(w, e));
 }
 
+// a += b for two compensated pairs (two-sum of the leading parts; the small parts
+// and the sum's rounding error accumulate in a.c).
+__device__ __forceinline__ void ff_add_ff(FF &a, const FF &b) {
+    ff_add(a, b.s);
+    a.c = __fadd_rn(a.c, b.c);
+}
+
+// Sum of a compensated pair over the 32 lanes of a warp (fixed shuffle tree; lane 0
+// holds the result).
+__device__ __forceinline__ FF ff_warp_sum(FF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF b;
+        b.s = __shfl_down_sync(0xffffffffu, a.s, o);
+        b.c = __shfl_down_sync(0xffffffffu, a.c, o);
+        ff_add_ff(a, b);
+    }
+    return a;
+}
+
 __device__ __forceinline__ double ff_value(const FF &a) { return (double)a.s + (double)a.c; }
 
 // ---------------------------------------------------------------------------

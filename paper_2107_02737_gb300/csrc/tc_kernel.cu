@@ -82,7 +82,8 @@ struct TcSmemTail {
     uint32_t pad;
     unsigned int issued;             // producer: ring stages this CTA has loaded into
     unsigned int consumed;           // MMA thread (even CTA): stages whose copies it has waited for
-    double red[EPI_WARPS][4];
+    FF red[EPI_WARPS][4];            // per epilogue warp: the tile's four partials (compensated pairs)
+    double flow_sums[4];             // dataflow: the previous layer's sums
     RoundCtl rc;
 };
 
@@ -624,9 +625,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         const float kc = w.flip ? al * (1.0f - 0.25f * al) : (1.0f - 0.5f * al) * (1.0f - 0.5f * al);
         const float kx1 = fmaf(2.0f * cf, ka, kb);
         // ||Y||_F^2 of the next operands equals ||X||_F^2 off the diagonal (y = x
-        // there); the diagonal difference y^2 - x^2 is added in FP64 (exact squares).
-        FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fp = {0.f, 0.f};
-        double dw = 0.0;
+        // there); the diagonal difference y^2 - x^2 is accumulated apart (exact squares).
+        FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fp = {0.f, 0.f}, fw = {0.f, 0.f};
         if (ok && rw0 < np) {
             // The chunks this warp finishes form one range [j0, j1): chunks entirely
             // below the diagonal come first, chunks past np last.
@@ -740,7 +740,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                                 if (r == c) ff_add(ft, x);
                                 if (dg) {
                                     ff_add(fp, P);
-                                    dw += (double)y * (double)y - (double)x * (double)x;
+                                    ff_add_sq(fw, y, 1.0f);
+                                    ff_add_sq(fw, x, -1.0f);
                                 }
                             }
                             // mirror (c, r), consecutive r across the warp; the diagonal
@@ -806,13 +807,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             acc_phase ^= 1u;
         }
         if (!w.resp) {
-            const double q = ff_value(fq);
-            double red4[4] = {ff_value(ft), q, q + dw, ff_value(fp)};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                for (int o = 16; o > 0; o >>= 1) red4[k] += __shfl_down_sync(0xffffffffu, red4[k], o);
+            // The tile's partials stay compensated FP32 pairs through the warp and
+            // cross-warp sums (FP64 arithmetic is slow on this part); one conversion.
+            FF qw = fq;
+            ff_add_ff(qw, fw);
+            const FF r4[4] = {ff_warp_sum(ft), ff_warp_sum(fq), ff_warp_sum(qw), ff_warp_sum(fp)};
             if (lane == 0)
-                for (int k = 0; k < 4; ++k) tl.red[ew][k] = red4[k];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) tl.red[ew][k] = r4[k];
             if (p.dataflow) {
                 // This warp's stores (generic proxy, and its tensor stores once
                 // complete) reach the TMA reads (async proxy) of any CTA that sees the
@@ -826,14 +828,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             }
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
             if (ew == 0 && lane == 0) {
+                FF a4[4] = {tl.red[0][0], tl.red[0][1], tl.red[0][2], tl.red[0][3]};
+                for (int k = 1; k < EPI_WARPS; ++k)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) ff_add_ff(a4[c], tl.red[k][c]);
                 Part s4;
-                s4.t = s4.q = s4.w = s4.p = 0.0;
-                for (int k = 0; k < EPI_WARPS; ++k) {
-                    s4.t += tl.red[k][0];
-                    s4.q += tl.red[k][1];
-                    s4.w += tl.red[k][2];
-                    s4.p += tl.red[k][3];
-                }
+                s4.t = ff_value(a4[0]);
+                s4.q = ff_value(a4[1]);
+                s4.w = ff_value(a4[2]);
+                s4.p = ff_value(a4[3]);
                 d.part[(w.n + 1) % 3][w.tile * CG + (int)rank] = s4;
                 if (p.dataflow) {
                     __threadfence();
@@ -875,7 +878,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             }
         } else {
             for (int r = 0;; ++r) {
-                if (!flow_decide(rc, p, tl.red[0], r, ew, lane, ntl * CG, abort)) {
+                if (!flow_decide(rc, p, tl.flow_sums, r, ew, lane, ntl * CG, abort)) {
                     tc_abort<CG>(rc, peer_abort);   // stop rule or error: halt this CTA and its peer
                     break;
                 }
