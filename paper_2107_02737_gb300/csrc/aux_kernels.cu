@@ -199,12 +199,24 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
     float *__restrict__ xf = xmaster(d, 0, false);
     uint16_t *__restrict__ op1 = d.xop;                    // hi
     uint16_t *__restrict__ op2 = d.xop + (size_t)np * np;  // lo
+    // ft: Tr X_0; fq: ||X_0||_F^2; fw (tensor-core path): ||Y_0||_F^2 - ||X_0||_F^2,
+    // which only the diagonal (y = x - 1/2 there) contributes.
     FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
     // Rows are strided over blocks, four consecutive columns per thread: no
     // index divisions on the hot loop; restrict-qualified so that the loads of
     // the next columns can be issued ahead of this group's stores.
     for (int i = blockIdx.x; i < np; i += gridDim.x) {
         const double *__restrict__ hrow = d.H + (size_t)(i < n ? i : 0) * n;
+        // The row's diagonal entry in FP64, once per row (FP64 is slow on this part),
+        // and its terms of the diagonal sums in the thread that stores it.
+        const float xdiag = (i < n) ? (float)((emax - hrow[i]) * inv) : 0.0f;
+        if (i < n && (int)threadIdx.x == (i % (AUX_THREADS * 4)) / 4) {
+            ff_add(ft, xdiag);
+            if (PATH == PATH_TC) {
+                ff_add_sq(fw, xdiag - 0.5f, 1.0f);
+                ff_add_sq(fw, xdiag, -1.0f);
+            }
+        }
 #pragma unroll 2
         for (int j0 = threadIdx.x * 4; j0 < np; j0 += AUX_THREADS * 4) {
             const size_t idx = (size_t)i * np + j0;
@@ -214,21 +226,23 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
                 const int j = j0 + q;
                 float v = 0.0f;
                 if (i < n && j < n) {
-                    if (i == j) {
-                        v = (float)((emax - hrow[j]) * inv);  // FP64 on the N diagonal entries only
-                    } else {
-                        float a, b;  // -h / (eps_max - eps_min): one rounding of a sum of small terms
-                        split_f64(hrow[j], a, b, bad_unused);
-                        v = -fmaf(a, inv_hi, fmaf(a, inv_lo, b * inv_lo24));
-                    }
+                    float a, b;  // -h / (eps_max - eps_min): one rounding of a sum of small terms
+                    split_f64(hrow[j], a, b, bad_unused);
+                    v = (i == j) ? xdiag : -fmaf(a, inv_hi, fmaf(a, inv_lo, b * inv_lo24));
                 }
                 x[q] = v;
                 y[q] = (i == j && i < n) ? v - 0.5f : v;
-                if (i == j) ff_add(ft, v);
                 ff_add_sq(fq, v, 1.0f);
-                if (PATH == PATH_TC) ff_add_sq(fw, y[q], 1.0f);
             }
-            *(float4 *)(xf + idx) = make_float4(x[0], x[1], x[2], x[3]);
+            if (PATH == PATH_SIMT || j0 + 3 <= i) {
+                *(float4 *)(xf + idx) = make_float4(x[0], x[1], x[2], x[3]);
+            } else if (j0 <= i) {
+                // The tensor-core layers and the output read the master's lower
+                // triangle and diagonal only.
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j0 + q <= i) xf[idx + q] = x[q];
+            }
             if (PATH == PATH_TC) {
                 // operands of the first square: the split of Y_0 = X_0 - I/2
                 uint16_t b[4], c[4];
@@ -239,6 +253,7 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
             }
         }
     }
+    if (PATH == PATH_TC) ff_add_ff(fw, fq);   // ||Y_0||_F^2
     double3 s = block_sum3(ff_value(ft), ff_value(fq), ff_value(fw));
     if (threadIdx.x == 0) {
         Part pr;
@@ -355,8 +370,7 @@ __global__ void __launch_bounds__(AUX_THREADS, 8) k_finalize(InstDesc *inst, int
     if (mode == MODE_ADJOINT) ys = (float)(-1.0 / (ctl->y_scale * (ctl->eps_max - ctl->eps_min)));
     // Tr[D H]: each H_ij unpacked to an FP32 pair (h1 + 2^-24 h2), x * h1 split exactly
     // into product and error (FMA), all summed in a compensated FP32 pair.
-    FF fe = {0.f, 0.f};
-    double tr = 0.0;
+    FF fe = {0.f, 0.f}, ftr = {0.f, 0.f};   // compensated FP32 pairs (FP64 is slow on this part)
     int bad_unused = 0;
     const int tc = threadIdx.x & 31, tr0 = threadIdx.x >> 5;   // tile column, first tile row
     const int nt = (n + 31) / 32;
@@ -377,7 +391,7 @@ __global__ void __launch_bounds__(AUX_THREADS, 8) k_finalize(InstDesc *inst, int
                 x = X[(size_t)i * np + j];
                 if (i == j) {
                     x += xoff;  // true X_L = stored X_L + c_L I
-                    tr += x;
+                    ff_add(ftr, x);
                 }
                 if (H) {
                     float h1, h2;
@@ -412,7 +426,7 @@ __global__ void __launch_bounds__(AUX_THREADS, 8) k_finalize(InstDesc *inst, int
         }
         __syncthreads();
     }
-    double2 s = block_sum2(ff_value(fe), tr);
+    double2 s = block_sum2(ff_value(fe), ff_value(ftr));
     if (threadIdx.x == 0) d.fin_part[blockIdx.x] = s;
 }
 
