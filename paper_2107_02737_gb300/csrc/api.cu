@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -160,7 +161,7 @@ struct Carver {
 // super-block, then row super-block, then column, then row) so that such a run
 // reads a compact set of row and column panels and the operand matrices, which
 // are larger than L2, are fetched from HBM about once per run.
-void build_tiles(int path, int np, int cg, std::vector<int2> &t) {
+void build_tiles_uncached(int path, int np, int cg, std::vector<int2> &t) {
     const int bm = (path == PATH_SIMT) ? SIMT_T : TC_BM * cg;
     const int bn = (path == PATH_SIMT) ? SIMT_T : TC_BN;
     const int nbi = (np + bm - 1) / bm, nbj = (np + bn - 1) / bn;  // a last pair tile may overhang np
@@ -177,10 +178,29 @@ void build_tiles(int path, int np, int cg, std::vector<int2> &t) {
     for (auto &k : keyed) t.push_back(k.second);
 }
 
+// The table for (path, np, cg) is built once per process (calls repeat the same sizes).
+void build_tiles(int path, int np, int cg, std::vector<int2> &t) {
+    static std::mutex mu;
+    static std::map<long long, std::vector<int2>> cache;
+    const long long key = ((long long)path * 4 + cg) * (1LL << 32) + np;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        std::vector<int2> v;
+        build_tiles_uncached(path, np, cg, v);
+        it = cache.emplace(key, std::move(v)).first;
+    }
+    t.insert(t.end(), it->second.begin(), it->second.end());
+}
+
+// Number of tiles of the table above, counted without building it.
 int ntiles_for(int path, int np, int cg) {
-    std::vector<int2> t;
-    build_tiles(path, np, cg, t);
-    return (int)t.size();
+    const int bm = (path == PATH_SIMT) ? SIMT_T : TC_BM * cg;
+    const int bn = (path == PATH_SIMT) ? SIMT_T : TC_BN;
+    const int nbi = (np + bm - 1) / bm, nbj = (np + bn - 1) / bn;
+    int count = 0;
+    for (int bj = 0; bj < nbj; ++bj) count += std::min(nbi, ((bj + 1) * bn + bm - 1) / bm);
+    return count;
 }
 
 // Partial records per layer: one per tile, per CTA of the tile.
@@ -379,25 +399,59 @@ struct Prepared {
 
 // Tensor-core tile shape and persistent grid for the plan: CTA pairs (M = 256)
 // when the device can co-schedule them, else single CTAs; `want` forces one.
+// Per device: its attributes and the persistent grid of each tile shape, queried
+// once per process (the occupancy queries cost more than a small solve's setup).
+struct LaunchGeometry {
+    bool known = false;
+    DeviceInfo di;
+    int grid_cg[3] = {0, 0, 0};
+    int simt_per_sm = 0;
+};
+bool launch_geometry(LaunchGeometry &g) {
+    static std::mutex mu;
+    static LaunchGeometry table[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    LaunchGeometry local;
+    LaunchGeometry &e = dev < 64 ? table[dev] : local;
+    if (!e.known) {
+        e.di = query_device();
+        if (e.di.err != cudaSuccess) return false;
+        if (e.di.major == 10 && e.di.minor == 3) {
+            e.grid_cg[2] = tc_grid_size(2, e.di.sm);
+            e.grid_cg[1] = tc_grid_size(1, e.di.sm);
+            e.simt_per_sm = simt_blocks_per_sm();
+        }
+        e.known = true;
+    }
+    g = e;
+    return true;
+}
+
 sp2_status choose_launch(Plan &pl, int want, int &grid) {
-    DeviceInfo di = query_device();
-    if (di.err != cudaSuccess) return SP2_ERR_CUDA;
+    LaunchGeometry geo;
+    if (!launch_geometry(geo)) return SP2_ERR_CUDA;
+    const DeviceInfo &di = geo.di;
     if (di.major != 10 || di.minor != 3) return SP2_ERR_UNSUPPORTED;
     if (pl.path == PATH_TC && !get_encode_fn()) return SP2_ERR_UNSUPPORTED;
     grid = 0;
     if (pl.path == PATH_TC) {
         if (want == 0 || want == 2) {
-            grid = tc_grid_size(2, di.sm);
+            grid = geo.grid_cg[2];
             pl.cg = 2;
         }
         if (grid <= 0) {
             if (want == 2) return SP2_ERR_UNSUPPORTED;
-            grid = tc_grid_size(1, di.sm);
+            grid = geo.grid_cg[1];
             pl.cg = 1;
         }
         if (grid <= 0) return SP2_ERR_UNSUPPORTED;
     } else {
-        const int per_sm = simt_blocks_per_sm();
+        const int per_sm = geo.simt_per_sm;
         if (per_sm <= 0) return SP2_ERR_UNSUPPORTED;
         grid = per_sm * di.sm;
     }
