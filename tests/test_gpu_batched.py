@@ -45,18 +45,20 @@ def test_batched_workload_64_instances():
     assert max(errs) <= TOL_D["bf16"]
 
 
-@pytest.mark.parametrize("cta_group", [1, 2])
-def test_dataflow_schedule_equals_barrier_schedule(cta_group):
+@pytest.mark.parametrize("n,precision,cta_group", [(4096, "fp16", 1), (4096, "fp16", 2), (1000, "fp16", 2),
+                                                   (2500, "bf16", 2), (1000, "bf16", 1)])
+def test_dataflow_schedule_equals_barrier_schedule(n, precision, cta_group):
     """A lone density solve runs its layers without a grid barrier between them (each
     K block waits for the tiles that wrote it, the decision waits for the whole layer);
     the same instance in a batch runs with the barrier.  Every tile's arithmetic is the
-    same, so D and every layer's statistics agree bit for bit, here over several waves
-    of tiles (N = 4096: 136 pair tiles, 272 single-CTA tiles)."""
-    ham = inputs.water_like_workload(4096)
+    same, so D and every layer's statistics agree bit for bit: over several waves of
+    tiles (N = 4096: 136 pair tiles, 272 single-CTA tiles) and at ragged sizes whose
+    last pair tiles overhang the padded matrix (N = 1000, 2500: N_p = 1024, 2560)."""
+    ham = inputs.water_like_workload(n) if n == 4096 else inputs.gapped_random(n, n // 2, inputs.rng_for(2, n))
     H = dev(ham.H)
-    D1, r1 = sp2.density(H, ham.n_occ, precision="fp16", cta_group=cta_group)
+    D1, r1 = sp2.density(H, ham.n_occ, precision=precision, cta_group=cta_group)
     small = inputs.gapped_random(128, 64, inputs.rng_for(2, 1))
-    Ds, res, status = sp2.density_batched([H, dev(small.H)], [ham.n_occ, 64], precision="fp16",
+    Ds, res, status = sp2.density_batched([H, dev(small.H)], [ham.n_occ, 64], precision=precision,
                                           cta_group=cta_group)
     assert status == sp2.OK and r1.converged
     assert r1.cta_group == cta_group
