@@ -329,7 +329,8 @@ sp2_status sp2_apply_layers(const float *X0, int N, const int *choices, int n_la
  *                       refinement layers, [2] the back-transformation and the FP64
  *                       Tr[D H], [3] all of it (CUDA events on the call's stream).
  * Allocates device memory for the FP64 and fixed-point matrices (about 50 bytes
- * per element plus the chain's workspace) and frees it before returning.
+ * per element) and for the chain's workspace, all before the first timed phase,
+ * and frees it before returning.
  * Returns SP2_ERR_NOT_CONVERGED also when X leaves [-2^-13, 1 + 2^-13]
  * spectrally during the refinement (its slices could not hold it exactly).
  */

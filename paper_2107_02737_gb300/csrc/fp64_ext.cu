@@ -266,6 +266,12 @@ sp2_status run_fp64(const double *H_in, const double *Z_in, int N, double n_occ,
     int *d_err = (int *)buf.get(64);
     double *d_rec = (double *)buf.get(sizeof(double) * 4 * 16 + 64);
     if (!X64 || !D32 || !part || !d_choice || !d_err || !d_rec) return SP2_ERR_NOMEM;
+    // The chain's workspace, with the call's other buffers (so that no allocation
+    // falls inside the timed phases), 256-byte aligned as sp2_density requires.
+    const size_t chain_bytes = sp2_density_workspace_bytes(N, &opt);
+    uint8_t *chain_raw = (uint8_t *)buf.get(chain_bytes + 256);
+    if (!chain_raw) return SP2_ERR_NOMEM;
+    void *chain_ws = (void *)(((uintptr_t)chain_raw + 255) & ~(uintptr_t)255);
     CKS(cudaMemsetAsync(d_err, 0, sizeof(int), s));
     CongruenceBufs cb;
     if (Z) {
@@ -294,7 +300,7 @@ sp2_status run_fp64(const double *H_in, const double *Z_in, int N, double n_occ,
     std::vector<sp2_layer_stat> lay(SP2_MAX_LAYERS_LIMIT + 16);
     local.layer = lay.data();
     local.layer_cap = (int)lay.size();
-    sp2_status r = sp2_density(Hc, N, n_occ, tol, D32, &local, &opt, nullptr, 0, s);
+    sp2_status r = sp2_density(Hc, N, n_occ, tol, D32, &local, &opt, chain_ws, chain_bytes, s);
     if (r != SP2_OK && r != SP2_ERR_NOT_CONVERGED) return r;
     const sp2_status chain_status = r;
     pe.mark(1, s);
