@@ -864,17 +864,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         // teardown.  Each tile's arithmetic, and so X and D, is that of the barrier
         // schedule bit for bit.
         const int ntl = p.inst[0].ntiles;
+        // When every pair has tiles in every layer, layer r's round-robin starts at a
+        // rotated position, so that the pairs holding one tile fewer change from
+        // layer to layer and the remainder tiles spread evenly over the chain (a
+        // tile's arithmetic does not depend on the pair that computes it).
+        const auto first_tile = [&](int r) {
+            return ntl >= nclusters ? (int)(((long long)cluster_id + (long long)r * (ntl % nclusters)) % nclusters)
+                                    : cluster_id;
+        };
         if (cluster_id >= ntl) {
             // no tiles here: only the epilogue warps take part (in the decisions)
         } else if (warp == 0) {
             if (lane == 0)
                 for (int r = 0; !*abort; ++r)
-                    for (int g = cluster_id; g < ntl && !*abort; g += nclusters) produce_tile(describe_flow(p, g, r));
+                    for (int g = first_tile(r); g < ntl && !*abort; g += nclusters) produce_tile(describe_flow(p, g, r));
         } else if (warp == 1) {
             if (lane == 0 && leader) {
                 bool ok = true;
                 for (int r = 0; ok && !*abort; ++r)
-                    for (int g = cluster_id; ok && g < ntl && !*abort; g += nclusters) ok = mma_tile(describe_flow(p, g, r));
+                    for (int g = first_tile(r); ok && g < ntl && !*abort; g += nclusters)
+                        ok = mma_tile(describe_flow(p, g, r));
             }
         } else {
             for (int r = 0;; ++r) {
@@ -882,7 +891,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     tc_abort<CG>(rc, peer_abort);   // stop rule or error: halt this CTA and its peer
                     break;
                 }
-                for (int g = cluster_id; g < rc.total; g += nclusters) epilogue_tile(describe(rc, p, g));
+                for (int g = first_tile(r); g < rc.total; g += nclusters) epilogue_tile(describe(rc, p, g));
             }
         }
     } else {
