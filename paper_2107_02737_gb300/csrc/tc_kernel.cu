@@ -925,15 +925,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
             __syncthreads();
             if (rc.abort || rc.total == 0) break;
 
+            // The round's tiles (largest instances first) are dealt to the pairs in a
+            // snake order, forward in even waves and backward in odd ones, which evens
+            // out the pairs' shares of large and small tiles.
+            const auto round_tile = [&](int k) {
+                return k * nclusters + ((k & 1) ? nclusters - 1 - cluster_id : cluster_id);
+            };
             if (warp == 0) {
                 if (lane == 0)
-                    for (int g = cluster_id; g < rc.total && !*abort; g += nclusters) produce_tile(describe(rc, p, g));
+                    for (int k = 0, g; (g = round_tile(k)) < rc.total && !*abort; ++k) produce_tile(describe(rc, p, g));
             } else if (warp == 1) {
                 if (lane == 0 && leader)
-                    for (int g = cluster_id; g < rc.total && !*abort; g += nclusters)
+                    for (int k = 0, g; (g = round_tile(k)) < rc.total && !*abort; ++k)
                         if (!mma_tile(describe(rc, p, g))) break;
             } else {
-                for (int g = cluster_id; g < rc.total; g += nclusters) epilogue_tile(describe(rc, p, g));
+                for (int k = 0, g; (g = round_tile(k)) < rc.total; ++k) epilogue_tile(describe(rc, p, g));
                 // This warp's tensor stores are complete; order this round's
                 // generic-proxy stores before the async-proxy (TMA) reads of the next
                 // round, on any SM.
