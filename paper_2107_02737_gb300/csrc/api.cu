@@ -732,6 +732,7 @@ sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
     rp.max_layers = P.o.max_layers;
     // Device hook: CTA 0 withholds its first barrier arrival (test_hook 1, or 3 in a CTA-pair launch).
     rp.test_hook = (P.o.test_hook == 1 || (P.o.test_hook == 3 && pl.path == PATH_TC && pl.cg == 2)) ? 1 : 0;
+    rp.publish = (pl.mode == MODE_DENSITY && pl.path == PATH_TC && !pl.dataflow) ? 1 : 0;
     if (pl.dataflow) {
         rp.dataflow = 1;
         rp.nblk = P.flow_nb;

@@ -258,19 +258,12 @@ __device__ __forceinline__ void round_ctl_init(RoundCtl &rc, const RunParams &p)
     rc.chist_a[0] = 1.0f;
 }
 
-// All threads of a CTA: sum, for every instance still running, the per-tile
-// partials of the layer just finished into sums[4 i .. 4 i + 3] (shared memory).
-// One warp per instance (warp w takes instances w, w + nwarps, ...): lane l adds
-// entries l, l + 32, ... in increasing order, then a fixed shuffle tree.  The
-// order depends only on the instance's own partials, so every CTA -- and a batch
-// or a lone call alike -- gets the same bits and takes the same decision.
-// One warp: the sums of instance i's partials of the layer just finished, lane l
-// adding entries l, l + 32, ... in increasing order, then a fixed shuffle tree
-// (valid in lane 0).
-__device__ __forceinline__ void sum_instance_partials(const RoundCtl &rc, const RunParams &p, int i, int lane,
-                                                      double (&a)[4]) {
+// One warp: the sums of instance i's partial records of layer n, lane l adding
+// entries l, l + 32, ... in increasing order, then a fixed shuffle tree (valid in
+// lane 0).  The order depends only on the instance's own records, so every CTA --
+// and a batch or a lone call alike -- gets the same bits and takes the same decision.
+__device__ __forceinline__ void sum_layer_partials(const RunParams &p, int i, int n, int lane, double (&a)[4]) {
     const InstDesc &d = p.inst[i];
-    const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
     const int cnt = (n == 0) ? d.ctl->init_parts : d.parts;
     const Part *part = d.part[n % 3];
     a[0] = a[1] = a[2] = a[3] = 0.0;
@@ -287,13 +280,45 @@ __device__ __forceinline__ void sum_instance_partials(const RoundCtl &rc, const 
         for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
 }
 
+// The sums of the layer instance i just finished.
+__device__ __forceinline__ void sum_instance_partials(const RoundCtl &rc, const RunParams &p, int i, int lane,
+                                                      double (&a)[4]) {
+    sum_layer_partials(p, i, rc.layer[i] + (rc.ran[i] ? 1 : 0), lane, a);
+}
+
+// All threads of a CTA: the sums, for every instance still running, of the
+// partials of the layer just finished into sums[4 i .. 4 i + 3] (shared memory),
+// one warp per instance (warp w takes instances w, w + nwarps, ...).  In a density
+// batch's round schedule the CTA that completed an instance's layer has already
+// published these sums (same function, same order, same bits): they are read back.
+// `sums` is followed by MAX_BATCH ints of scratch (the decision's buffer, free here).
 __device__ inline void reduce_round_partials(const RoundCtl &rc, const RunParams &p, double *sums) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (rc.phase == 1) return;
+    int *got = (int *)(sums + 4 * MAX_BATCH);
+    // Published sums first, one thread per instance, every load in flight at once.
+    for (int i = threadIdx.x; i < p.B; i += blockDim.x) {
+        int ok = 0;
+        const int n = rc.layer[i] + (rc.ran[i] ? 1 : 0);
+        if (p.publish && rc.active[i] && n > 0) {
+            const InstCtl *ctl = p.inst[i].ctl;
+            const int pn = __ldcg(&ctl->psum_n);
+            double v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = __ldcg(&ctl->psum[c]);
+            if (pn == n) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sums[i * 4 + c] = v[c];
+                ok = 1;
+            }
+        }
+        got[i] = ok;
+    }
+    __syncthreads();
     for (int i = wid; i < p.B; i += nw) {
-        if (!rc.active[i]) continue;
+        if (!rc.active[i] || got[i]) continue;
         double a[4];
-        sum_instance_partials(rc, p, i, lane, a);
+        sum_layer_partials(p, i, rc.layer[i] + (rc.ran[i] ? 1 : 0), lane, a);
         if (lane == 0)
             for (int c = 0; c < 4; ++c) sums[i * 4 + c] = a[c];
     }

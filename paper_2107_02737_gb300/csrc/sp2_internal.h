@@ -77,6 +77,12 @@ struct InstCtl {
     unsigned long long ymax_key;
     int nonfinite, status, layers, stop_reason;
     int final_x, final_y, init_parts, degenerate;
+    // Round schedule of a density batch: the CTA that completes an instance's last
+    // tile of layer n sums the layer's partial records (the same fixed order as
+    // every CTA's own sum) and publishes them here, tagged with n.
+    unsigned int psum_done;                  // CTA-tile completions over all layers
+    int psum_n;                              // layer of psum (0: none yet)
+    double psum[4];
     LayerStatDev stat[MAX_L + 1];
 };
 
@@ -123,6 +129,7 @@ struct RunParams {
     int test_hook;                    // 1: CTA 0 withholds its first barrier arrival (dataflow:
                                       // its first tile completion)
     int dataflow;                     // 1: no grid barrier between layers (see the tensor-core kernel)
+    int publish;                      // 1: round schedule of a density batch, sums published per layer
     int nblk;                         // dataflow: 256-row blocks of X (round_up(np, 256) / 256)
     unsigned int *tile_done;          // dataflow: per tile, CTA completions over all layers
     unsigned int *layer_done;         // dataflow: CTA-tile completions over all layers

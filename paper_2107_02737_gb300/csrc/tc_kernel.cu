@@ -849,6 +849,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
                     flow_first = false;
                 }
             }
+            if (p.publish && ew == 0) {
+                // Round schedule of a density batch: the CTA whose record completes the
+                // instance's layer sums it (the order of every CTA's own sum) and
+                // publishes the sums for the decision after the grid barrier.
+                int last = 0;
+                if (lane == 0) {
+                    __threadfence();
+                    const unsigned int target = (unsigned int)(w.n + 1) * (unsigned int)d.parts;
+                    last = (atomicAdd(&d.ctl->psum_done, 1u) + 1u == target) ? 1 : 0;
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence();   // the other CTAs' records, released before their increments
+                    double a[4];
+                    sum_layer_partials(p, w.inst, w.n + 1, lane, a);
+                    if (lane == 0) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) d.ctl->psum[c] = a[c];
+                        d.ctl->psum_n = w.n + 1;
+                    }
+                }
+            }
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
         }
     };
