@@ -949,19 +949,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
 
             // The round's tiles (largest instances first) are dealt to the pairs in a
             // snake order, forward in even waves and backward in odd ones, which evens
-            // out the pairs' shares of large and small tiles.
+            // out the pairs' shares of large and small tiles; each pair then takes its
+            // share smallest first, so that the epilogues of its small tiles overlap
+            // the MMAs of the large ones after them.
             const auto round_tile = [&](int k) {
                 return k * nclusters + ((k & 1) ? nclusters - 1 - cluster_id : cluster_id);
             };
+            int nk = 0;
+            while (round_tile(nk) < rc.total) ++nk;
             if (warp == 0) {
                 if (lane == 0)
-                    for (int k = 0, g; (g = round_tile(k)) < rc.total && !*abort; ++k) produce_tile(describe(rc, p, g));
+                    for (int k = nk - 1; k >= 0 && !*abort; --k) produce_tile(describe(rc, p, round_tile(k)));
             } else if (warp == 1) {
                 if (lane == 0 && leader)
-                    for (int k = 0, g; (g = round_tile(k)) < rc.total && !*abort; ++k)
-                        if (!mma_tile(describe(rc, p, g))) break;
+                    for (int k = nk - 1; k >= 0 && !*abort; --k)
+                        if (!mma_tile(describe(rc, p, round_tile(k)))) break;
             } else {
-                for (int k = 0, g; (g = round_tile(k)) < rc.total; ++k) epilogue_tile(describe(rc, p, g));
+                for (int k = nk - 1; k >= 0; --k) epilogue_tile(describe(rc, p, round_tile(k)));
                 // This warp's tensor stores are complete; order this round's
                 // generic-proxy stores before the async-proxy (TMA) reads of the next
                 // round, on any SM.
