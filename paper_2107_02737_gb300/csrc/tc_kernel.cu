@@ -886,13 +886,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_persistent(const __grid_co
         // teardown.  Each tile's arithmetic, and so X and D, is that of the barrier
         // schedule bit for bit.
         const int ntl = p.inst[0].ntiles;
-        // When every pair has tiles in every layer, layer r's round-robin starts at a
-        // rotated position, so that the pairs holding one tile fewer change from
-        // layer to layer and the remainder tiles spread evenly over the chain (a
-        // tile's arithmetic does not depend on the pair that computes it).
+        // When every pair has a few tiles in every layer (fewer than four), layer r's
+        // round-robin starts at a rotated position, so that the pairs holding one
+        // tile fewer change from layer to layer and the remainder tiles spread evenly
+        // over the chain (a tile's arithmetic does not depend on the pair that
+        // computes it).  With more tiles per pair the imbalance is small and the fixed
+        // assignment keeps more of the operand panels in L2.
+        const bool rotate = (ntl >= nclusters && ntl < 4 * nclusters);
         const auto first_tile = [&](int r) {
-            return ntl >= nclusters ? (int)(((long long)cluster_id + (long long)r * (ntl % nclusters)) % nclusters)
-                                    : cluster_id;
+            return rotate ? (int)(((long long)cluster_id + (long long)r * (ntl % nclusters)) % nclusters) : cluster_id;
         };
         if (cluster_id >= ntl) {
             // no tiles here: only the epilogue warps take part (in the decisions)
