@@ -39,7 +39,8 @@
  *  - Calls are stream-ordered on `stream` (a cudaStream_t; NULL = legacy
  *    default stream) and synchronise that stream before returning, because
  *    the status and the statistics are read back to the host.
- *  - A wait inside a kernel (the grid barrier between layers, a pipeline
+ *  - A wait inside a kernel (the grid barrier between layers; in a single
+ *    density solve, the wait for the tiles of the previous layer; a pipeline
  *    barrier) that exceeds `timeout_ms` makes the kernel stop and the call
  *    return SP2_ERR_TIMEOUT; no call leaves a kernel spinning.
  *  - Errors never leave partially written output undefined in size: on any
@@ -135,8 +136,8 @@ typedef struct {
                              tile (cooperative launch), 2 = a CTA pair per 256 x 256 tile
                              (M = 256 MMAs; a cluster launch sized to the pairs the device
                              holds at once: work running concurrently on the same GPU can
-                             deny that residency, and the grid barrier then runs out after
-                             timeout_ms -- with cta_group = 0 the call is then retried once
+                             deny that residency, and the waits between layers then run out
+                             after timeout_ms -- with cta_group = 0 the call is then retried once
                              with single-CTA tiles, with cta_group = 2 it returns
                              SP2_ERR_TIMEOUT; batch plans do not retry) */
     int accelerate;       /* 1 = accelerated chain from an estimated interval [eps_homo, eps_lumo]

@@ -823,7 +823,8 @@ sp2_status run_plan_once(Plan &pl, double tol, const sp2_opts &o, void *ws, size
 
 // A CTA-pair launch relies on every pair being resident at once (it is a cluster
 // launch, not a cooperative one); work running concurrently on the same GPU can
-// deny that, and the grid barrier then runs out of time.  When the tile shape was
+// deny that, and the waits between layers (the grid barrier, or the dataflow
+// schedule's waits for the previous layer's tiles) then run out of time.  When the tile shape was
 // left to the library, the call is retried once with single-CTA tiles, whose
 // cooperative launch guarantees co-residency.
 sp2_status run_plan(Plan &pl, double tol, const sp2_opts &o, void *ws, size_t ws_bytes, cudaStream_t s) {

@@ -36,8 +36,14 @@
 //               lanes 32 (w mod 4) .. +31 and the tile's column half (w - 2) / 4, in
 //               16-column chunks; X_{n+1} = S or 2 X_n - S, FP32 master + split
 //               operands written for the tile and its mirror (only tiles with rows <=
-//               columns are computed), compensated FP64 partials of Tr X and ||X||_F^2.
-// Between layers: grid barrier, then every CTA takes the same layer decision.
+//               columns are computed; the direct orientation of a chunk above the
+//               diagonal leaves as two TMA tensor stores), compensated partials of
+//               Tr X and ||X||_F^2 (FP32 pairs, one FP64 record per tile and CTA).
+// Between layers, two schedules.  A single density solve runs without a grid
+// barrier (dataflow): each tile of layer n + 1 starts its K blocks once the tiles
+// of layer n that wrote them have completed, and the epilogue warps alone wait for
+// the whole layer to take its decision.  Batches, responses and adjoints run in
+// rounds ended by a grid barrier, after which every CTA takes the same decisions.
 // The response / adjoint stream reuses the same machinery with six products per K
 // block: (C + C^T)[i,j] = sum_k X[i,k] Y[j,k] + Y[i,k] X[j,k] for symmetric X and Y.
 #include "device_common.cuh"

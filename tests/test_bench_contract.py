@@ -67,3 +67,21 @@ def test_l2_note_states_whether_inputs_exceed_l2(n, big):
     note = bench.l2_note(n)
     assert note.startswith("inputs larger than L2" if big else "inputs NOT larger than L2")
     assert f"{n * n * 8 / 1e6:.0f} MB FP64" in note
+
+
+def test_executed_flops_count_the_upper_triangle_tiles():
+    """The roofline's executed rate counts every tile with at least one element on or
+    above the diagonal (256 x 256 for CTA pairs, 128 x 256 for single CTAs, the last
+    tiles overhanging the padded size) and three split products per tile and layer."""
+    import bench
+
+    def enumerate_tiles(n, bm, bn=256):
+        np_ = -(-n // 128) * 128
+        return sum(1 for bj in range(-(-np_ // bn)) for bi in range(-(-np_ // bm)) if bi * bm < (bj + 1) * bn), np_
+
+    for n in (128, 300, 1000, 4096, 8192):
+        for cg, bm in ((2, 256), (1, 128)):
+            t, np_ = enumerate_tiles(n, bm)
+            assert bench.chain_executed_flops(n, 3, cg) == 3 * t * 3 * 2.0 * bm * 256 * np_
+    # N = 8192 with CTA pairs: 528 tiles per layer, 5.44e13 flops over 32 layers
+    assert bench.chain_executed_flops(8192, 32, 2) == 32 * 528 * 3 * 2.0 * 256 * 256 * 8192
