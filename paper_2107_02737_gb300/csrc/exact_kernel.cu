@@ -152,7 +152,8 @@ __device__ __forceinline__ bool make_slices(long long v, int slices, int beta, i
             const long long a = (v + (1ll << (sh - 1))) >> sh;   // sh >= 1: callers keep a bit below the last slice
             v -= a << sh;
             if (s == 0 && (a > 2048 || a < -2048)) ok = false;
-            out[s] = __half_as_ushort(__float2half_rn((float)a));
+            // |a| <= 2^11 for the leading slice, <= 2^beta after it: exact through int32 and FP16
+            out[s] = __half_as_ushort(__int2half_rn((int)a));
             sh -= beta;
         } else {
             out[s] = 0;
@@ -641,7 +642,9 @@ __global__ void __launch_bounds__(XT) k_xs_init_sp2(const float *__restrict__ D,
         const long long f = fixed_of_float(d, unit) - (dg ? half_unit : 0ll);
         uint16_t a[XS_MAX_SLICES];
         if (!make_slices(f, slices, beta, unit - 12, a)) bad = 1;
-        for (int s = 0; s < slices; ++s) sl[(size_t)s * mat + (size_t)r * np + c] = a[s];
+#pragma unroll
+        for (int s = 0; s < XS_MAX_SLICES; ++s)
+            if (s < slices) sl[(size_t)s * mat + (size_t)r * np + c] = a[s];
         if (c <= r) y[(size_t)r * np + c] = f;
         if (dg) {
             const double yv = (double)d - 0.5;
@@ -759,7 +762,9 @@ __global__ void k_xs_slice_rows(const double *__restrict__ M, int n, int np, int
         const double x = (row < n && k < n) ? M[(size_t)row * n + k] : 0.0;
         uint16_t a[XS_MAX_SLICES];
         if (!make_slices(__double2ll_rn(x * sc), slices, beta, beta * (slices - 1) + 1, a)) bad = 1;
-        for (int s = 0; s < slices; ++s) sl[(size_t)s * mat + (size_t)row * np + k] = a[s];
+#pragma unroll
+        for (int s = 0; s < XS_MAX_SLICES; ++s)
+            if (s < slices) sl[(size_t)s * mat + (size_t)row * np + k] = a[s];
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(err, SP2_ERR_NOT_CONVERGED);
 }
