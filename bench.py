@@ -354,7 +354,8 @@ def main():
     ms_local = ev0.elapsed_time(ev1) / args.steps
     res = results[-1]
     L = res.layers
-    launches_per_step = 5  # Gershgorin, input layer, persistent layer kernel, output copy, final reduction
+    # Gershgorin (two passes), input layer, persistent layer kernel, output copy, final reduction
+    launches_per_step = 6
     # Replicas: every rank solves its own copy; the whole-job rate is the work of
     # all ranks over the slowest rank's step time.
     from paper_2107_02737_gb300 import shard

@@ -276,15 +276,27 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
     (void)offsets_unused;
     Carver c(nullptr);
     const int B = (int)pl.inst.size();
+    // The upload region (the order of prepare()): what the host writes before a launch.
+    c.take(64);                           // barrier, error word, dataflow layer counter
+    c.take(sizeof(InstCtl) * B);          // control blocks
+    c.take(sizeof(InstCtl) * B);          // their initial state, copied in before every replay
     c.take(sizeof(InstDesc) * B);
     int tiles = 0;
     for (auto &s : pl.inst) tiles += ntiles_for(pl.path, round_up(s.n, PAD), pl.cg);
     c.take(sizeof(int2) * tiles);
-    c.take(64);                           // barrier + err
     c.take(sizeof(int) * (MAX_L + 1));    // forced choices
     c.take(sizeof(double) * (MAX_L + 1)); // forced expansions
-    c.take(sizeof(InstCtl) * B);          // control blocks
-    c.take(sizeof(InstCtl) * B);          // their initial state, copied in before every launch
+    for (int i = 0; i < B; ++i) {
+        const int np = round_up(pl.inst[i].n, PAD);
+        if (pl.dataflow) {
+            c.take(sizeof(unsigned int) * ntiles_for(pl.path, np, pl.cg));      // tile completions
+            c.take(sizeof(int) * 2 * (size_t)flow_nblk(np) * flow_nblk(np));  // block sources
+        }
+        if (pl.path == PATH_TC) {
+            c.take((size_t)pl.slots[i] * MAPS_PER_SLOT * sizeof(CUtensorMap));
+            if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT) c.take(2 * MAPS_PER_SLOT * sizeof(CUtensorMap));
+        }
+    }
     const int initb = init_blocks_host(pl.max_np);
     for (int i = 0; i < B; ++i) {
         const int np = round_up(pl.inst[i].n, PAD);
@@ -293,16 +305,11 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
         c.take(sizeof(Part) * cap);
         c.take(sizeof(Part) * cap);
         c.take(sizeof(Part) * cap);
-        if (pl.dataflow) {
-            c.take(sizeof(unsigned int) * ntiles_for(pl.path, np, pl.cg));      // tile completions
-            c.take(sizeof(int) * 2 * (size_t)flow_nblk(np) * flow_nblk(np));  // block sources
-        }
         c.take(sizeof(double2) * FIN_BLOCKS_MAX);
         c.take(mat * 4);
         c.take(mat * 4);
         if (pl.path == PATH_TC) {
             c.take((size_t)pl.slots[i] * 2 * mat * 2);
-            c.take((size_t)pl.slots[i] * MAPS_PER_SLOT * sizeof(CUtensorMap));
             if (pl.ckpt_s[i] > 0) {
                 c.take((size_t)pl.ckpt_k[i] * mat * 4);
                 c.take(mat * 4);
@@ -312,7 +319,6 @@ size_t plan_bytes(const Plan &pl, std::vector<size_t> *offsets_unused = nullptr)
                 c.take(mat * 4);
                 c.take(mat * 4);
                 c.take(2 * 2 * mat * 2);
-                c.take(2 * MAPS_PER_SLOT * sizeof(CUtensorMap));
             }
         }
     }
@@ -390,9 +396,12 @@ struct Prepared {
     unsigned int *d_tile_done = nullptr;   // dataflow: per-tile completion counters
     int *d_blk_src = nullptr;              // dataflow: block sources
     int flow_tiles = 0, flow_nb = 0;
+    int fin_blocks = 0;              // output kernel blocks per instance
     InstCtl *d_ctl = nullptr;        // B live control blocks
     InstCtl *d_ctl_init = nullptr;   // B initial control blocks
     std::vector<InstCtl> h_ctl;
+    std::vector<uint8_t> h_upload;   // host image of the upload region
+    std::vector<uint8_t> h_back;     // barrier and error words and control blocks, read back
     std::vector<std::pair<float *, float *>> copy_back;  // (host, device staging)
     std::vector<size_t> copy_back_n;
 };
@@ -470,6 +479,12 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
     P.tol = tol;
     const int B = (int)pl.inst.size();
     Carver c(ws);
+    // The upload region comes first and is contiguous: one host-to-device copy
+    // writes all of it (the zeroed counters included).  The control blocks follow
+    // the barrier and error word, so that one copy also reads both back.
+    uint8_t *d_sync = (uint8_t *)c.take(64);
+    InstCtl *d_ctl = (InstCtl *)c.take(sizeof(InstCtl) * B);
+    InstCtl *d_ctl_init = (InstCtl *)c.take(sizeof(InstCtl) * B);
     InstDesc *d_inst = (InstDesc *)c.take(sizeof(InstDesc) * B);
     std::vector<std::vector<int2>> tiles(B);
     int total_tiles = 0;
@@ -478,21 +493,42 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         total_tiles += (int)tiles[i].size();
     }
     int2 *d_tiles = (int2 *)c.take(sizeof(int2) * total_tiles);
-    uint8_t *d_sync = (uint8_t *)c.take(64);
     int *d_forced = (int *)c.take(sizeof(int) * (MAX_L + 1));
     double *d_forced_alpha = (double *)c.take(sizeof(double) * (MAX_L + 1));
-    InstCtl *d_ctl = (InstCtl *)c.take(sizeof(InstCtl) * B);
-    InstCtl *d_ctl_init = (InstCtl *)c.take(sizeof(InstCtl) * B);
+    std::vector<CUtensorMap *> d_xmaps(B, nullptr), d_ymaps(B, nullptr);
+    std::vector<int *> d_src(B, nullptr);
+    for (int i = 0; i < B; ++i) {
+        const int np = round_up(pl.inst[i].n, PAD);
+        if (pl.dataflow) {
+            P.flow_tiles = (int)tiles[i].size();
+            P.flow_nb = flow_nblk(np);
+            P.d_tile_done = (unsigned int *)c.take(sizeof(unsigned int) * tiles[i].size());
+            d_src[i] = (int *)c.take(sizeof(int) * 2 * (size_t)P.flow_nb * P.flow_nb);
+            P.d_blk_src = d_src[i];
+        }
+        if (pl.path == PATH_TC) {
+            d_xmaps[i] = (CUtensorMap *)c.take((size_t)pl.slots[i] * MAPS_PER_SLOT * sizeof(CUtensorMap));
+            if (pl.mode == MODE_RESPONSE || pl.mode == MODE_ADJOINT)
+                d_ymaps[i] = (CUtensorMap *)c.take(2 * MAPS_PER_SLOT * sizeof(CUtensorMap));
+        }
+    }
+    const size_t upload_bytes = c.off;
+    std::vector<uint8_t> &blob = P.h_upload;
+    blob.assign(upload_bytes, 0);
+    auto put = [&](const void *dev, const void *host, size_t bytes) {
+        if (bytes) memcpy(blob.data() + ((const uint8_t *)dev - (const uint8_t *)ws), host, bytes);
+    };
 
     std::vector<InstDesc> h_inst(B);
     std::vector<InstCtl> &h_ctl = P.h_ctl;
     h_ctl.assign(B, InstCtl());
     std::vector<int2> h_tiles;
     std::vector<std::vector<CUtensorMap>> h_xmaps(B), h_ymaps(B);
-    std::vector<CUtensorMap *> d_xmaps(B, nullptr), d_ymaps(B, nullptr);
     std::vector<int> forced;
     std::vector<double> forced_alpha;
     const int initb = init_blocks_host(pl.max_np);
+    P.fin_blocks = finalize_blocks();
+    if (P.fin_blocks < 1) return SP2_ERR_CUDA;
     bool user_bounds = o.user_bounds != 0;
 
     for (int i = 0; i < B; ++i) {
@@ -514,26 +550,21 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         d.nforced = -1;
         d.nslots_x = pl.slots[i];
         d.part_cap = std::max(d.parts, initb);
-        d.fin_blocks = FIN_BLOCKS_MAX;
+        d.fin_blocks = P.fin_blocks;
         d.ctl = d_ctl + i;
         d.part[0] = (Part *)c.take(sizeof(Part) * d.part_cap);
         d.part[1] = (Part *)c.take(sizeof(Part) * d.part_cap);
         d.part[2] = (Part *)c.take(sizeof(Part) * d.part_cap);
         if (pl.dataflow) {
-            P.flow_tiles = d.ntiles;
-            P.flow_nb = flow_nblk(np);
-            P.d_tile_done = (unsigned int *)c.take(sizeof(unsigned int) * d.ntiles);
-            P.d_blk_src = (int *)c.take(sizeof(int) * 2 * (size_t)P.flow_nb * P.flow_nb);
             std::vector<int> src;
             build_block_sources(np, pl.cg, tiles[i], src);
-            CK(cudaMemcpyAsync(P.d_blk_src, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, s));
+            put(d_src[i], src.data(), sizeof(int) * src.size());
         }
         d.fin_part = (double2 *)c.take(sizeof(double2) * FIN_BLOCKS_MAX);
         d.xf[0] = (float *)c.take(mat * 4);
         d.xf[1] = (float *)c.take(mat * 4);
         if (pl.path == PATH_TC) {
             d.xop = (uint16_t *)c.take((size_t)d.nslots_x * 2 * mat * 2);
-            d_xmaps[i] = (CUtensorMap *)c.take((size_t)d.nslots_x * MAPS_PER_SLOT * sizeof(CUtensorMap));
             d.xmap = d_xmaps[i];
             h_xmaps[i].resize((size_t)d.nslots_x * MAPS_PER_SLOT);
             // Per slot: the K segments' operands op0, op1, op2 = hi, hi, lo over the
@@ -553,7 +584,6 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
                 d.yf[0] = (float *)c.take(mat * 4);
                 d.yf[1] = (float *)c.take(mat * 4);
                 d.yop = (uint16_t *)c.take(2 * 2 * mat * 2);
-                d_ymaps[i] = (CUtensorMap *)c.take(2 * MAPS_PER_SLOT * sizeof(CUtensorMap));
                 d.ymap = d_ymaps[i];
                 h_ymaps[i].resize(2 * MAPS_PER_SLOT);
                 for (int sl = 0; sl < 2; ++sl)
@@ -673,23 +703,19 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
         }
     }
 
-    // Upload descriptors, tables, tensor maps and the initial control blocks.
-    CK(cudaMemcpyAsync(d_inst, h_inst.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_tiles, h_tiles.data(), sizeof(int2) * h_tiles.size(), cudaMemcpyHostToDevice, s));
-    if (!forced.empty())
-        CK(cudaMemcpyAsync(d_forced, forced.data(), sizeof(int) * forced.size(), cudaMemcpyHostToDevice, s));
-    if (!forced_alpha.empty())
-        CK(cudaMemcpyAsync(d_forced_alpha, forced_alpha.data(), sizeof(double) * forced_alpha.size(),
-                           cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_ctl_init, h_ctl.data(), sizeof(InstCtl) * B, cudaMemcpyHostToDevice, s));
+    // Upload descriptors, tables, tensor maps and the initial control blocks (live and
+    // kept) in one copy; the barrier word, error word and completion counters go up as zeros.
+    put(d_inst, h_inst.data(), sizeof(InstDesc) * B);
+    put(d_tiles, h_tiles.data(), sizeof(int2) * h_tiles.size());
+    put(d_forced, forced.data(), sizeof(int) * forced.size());
+    put(d_forced_alpha, forced_alpha.data(), sizeof(double) * forced_alpha.size());
+    put(d_ctl, h_ctl.data(), sizeof(InstCtl) * B);
+    put(d_ctl_init, h_ctl.data(), sizeof(InstCtl) * B);
     for (int i = 0; i < B; ++i) {
-        if (d_xmaps[i])
-            CK(cudaMemcpyAsync(d_xmaps[i], h_xmaps[i].data(), h_xmaps[i].size() * sizeof(CUtensorMap),
-                               cudaMemcpyHostToDevice, s));
-        if (d_ymaps[i])
-            CK(cudaMemcpyAsync(d_ymaps[i], h_ymaps[i].data(), h_ymaps[i].size() * sizeof(CUtensorMap),
-                               cudaMemcpyHostToDevice, s));
+        if (d_xmaps[i]) put(d_xmaps[i], h_xmaps[i].data(), h_xmaps[i].size() * sizeof(CUtensorMap));
+        if (d_ymaps[i]) put(d_ymaps[i], h_ymaps[i].data(), h_ymaps[i].size() * sizeof(CUtensorMap));
     }
+    CK(cudaMemcpyAsync(ws, blob.data(), upload_bytes, cudaMemcpyHostToDevice, s));
     P.user_bounds = user_bounds;
     P.d_inst = d_inst;
     P.d_tiles = d_tiles;
@@ -700,13 +726,16 @@ sp2_status prepare(Prepared &P, const sp2_opts &o, double tol, void *ws, size_t 
 }
 
 // One solve on stream s: reset, input layer, the persistent layer kernel, the
-// output.  ev (optional, 4 events) brackets the phases.
-sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
+// output.  ev (optional, 4 events) brackets the phases.  `fresh`: the upload of
+// prepare() is the last write to the control state, so the reset is already done.
+sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev, bool fresh = false) {
     const Plan &pl = P.pl;
     const int B = (int)pl.inst.size();
-    CK(cudaMemcpyAsync(P.d_ctl, P.d_ctl_init, sizeof(InstCtl) * B, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(P.d_sync, 0, 64, s));
-    if (pl.dataflow) CK(cudaMemsetAsync(P.d_tile_done, 0, sizeof(unsigned int) * P.flow_tiles, s));
+    if (!fresh) {
+        CK(cudaMemcpyAsync(P.d_ctl, P.d_ctl_init, sizeof(InstCtl) * B, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(P.d_sync, 0, 64, s));
+        if (pl.dataflow) CK(cudaMemsetAsync(P.d_tile_done, 0, sizeof(unsigned int) * P.flow_tiles, s));
+    }
     if (ev) CK(cudaEventRecord(ev[0], s));
     if (pl.mode == MODE_APPLY) {
         CK(launch_init_x_from(P.d_inst, pl.inst[0].X0, pl.max_np, pl.path, pl.precision, s));
@@ -743,7 +772,7 @@ sp2_status enqueue(const Prepared &P, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) CK(cudaEventRecord(ev[1], s));
     CK(pl.path == PATH_TC ? launch_tc_persistent(rp, pl.cg, P.grid, s) : launch_simt_persistent(rp, P.grid, s));
     if (ev) CK(cudaEventRecord(ev[2], s));
-    CK(launch_finalize(P.d_inst, B, pl.max_n, pl.mode == MODE_APPLY ? MODE_DENSITY : pl.mode, s));
+    CK(launch_finalize(P.d_inst, B, P.fin_blocks, pl.mode == MODE_APPLY ? MODE_DENSITY : pl.mode, s));
     if (ev) CK(cudaEventRecord(ev[3], s));
     return SP2_OK;
 }
@@ -755,10 +784,14 @@ sp2_status collect(Prepared &P, cudaStream_t s, const float *ph) {
     for (size_t k = 0; k < P.copy_back.size(); ++k)
         CK(cudaMemcpyAsync(P.copy_back[k].first, P.copy_back[k].second, P.copy_back_n[k] * 4,
                            cudaMemcpyDeviceToHost, s));
-    int h_err = 0;
-    CK(cudaMemcpyAsync(&h_err, P.d_sync + 4, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(P.h_ctl.data(), P.d_ctl, sizeof(InstCtl) * B, cudaMemcpyDeviceToHost, s));
+    // The error word and the control blocks in one copy (they are adjacent).
+    const size_t ctl_off = (size_t)((const uint8_t *)P.d_ctl - P.d_sync);
+    P.h_back.resize(ctl_off + sizeof(InstCtl) * B);
+    CK(cudaMemcpyAsync(P.h_back.data(), P.d_sync, P.h_back.size(), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    int h_err = 0;
+    memcpy(&h_err, P.h_back.data() + 4, sizeof(int));
+    memcpy(P.h_ctl.data(), P.h_back.data() + ctl_off, sizeof(InstCtl) * B);
     if (h_err) return (sp2_status)h_err;
     int worst = SP2_OK;
     for (int i = 0; i < B; ++i) {
@@ -805,7 +838,7 @@ sp2_status run_plan_once(Plan &pl, double tol, const sp2_opts &o, void *ws, size
     } ev_guard{ev};
     if (o.profile)
         for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ev[k]));
-    r = enqueue(P, s, o.profile ? ev : nullptr);
+    r = enqueue(P, s, o.profile ? ev : nullptr, true);
     if (r != SP2_OK) return r;
     float ph[4] = {0.f, 0.f, 0.f, 0.f};
     r = collect(P, s, nullptr);

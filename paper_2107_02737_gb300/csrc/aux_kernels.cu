@@ -1,9 +1,13 @@
 // aux_kernels.cu -- the HBM-bound steps around the layer loop:
-//   * Gershgorin spectral bounds of H in FP64 (one read pass over H),
+//   * Gershgorin spectral bounds of H in FP64 (one read of H's lower triangle,
+//     then one FP64 sum per row),
 //   * the input layer X_0 = (eps_max I - H)/(eps_max - eps_min) with its FP32
-//     master, split operands and FP64 trace partials (one read of H, one write of X),
+//     master, split operands and FP64 trace partials (one read of H's lower
+//     triangle, one write of X),
 //   * the response / adjoint stream start Y_0 (scaled by a power of two),
 //   * the output copy D = X_L with FP64 Tr[D H] and Tr D.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace sp2i {
@@ -13,14 +17,18 @@ namespace {
 constexpr int AUX_THREADS = 256;
 
 // ---------------------------------------------------------------------------
-// FP64 -> FP32 pairs with 32-bit integer operations only.  GB300 runs FP64
-// arithmetic and FP64 <-> FP32 conversions at a small fraction of its FP32 and
+// FP64 -> FP32 pairs with 32-bit integer and FP32 operations only.  GB300 runs
+// FP64 arithmetic and its conversion instructions (FP64 <-> FP32, integer ->
+// float, FP32 -> FP16 one value at a time) at a small fraction of its FP32 and
 // integer rates, so the HBM-bound kernels that read FP64 matrices unpack them
 // here.  split_f64(v, hi, lo24): hi = v with its mantissa truncated to 24
 // bits, lo24 = 2^24 x (the next 24 bits, truncated), so that
 // 0 <= |v| - (|hi| + 2^-24 |lo24|) < 2^-47 |v| for |v| >= 2^-98; below that
 // lo24 is 0 and the cut is < 2^-121.  The 2^24 keeps lo24 a normal float.
-// Values below 2^-126 give hi = 0; non-finite inputs and |v| >= 2^128 set `bad`.
+// The 24-bit integer becomes a float exactly by the exponent-field identity
+// float(2^23 + m) = bits(0x4B000000 | m) for m < 2^23, and one more exact add
+// for its top bit.  Values below 2^-126 give hi = 0; non-finite inputs and
+// |v| >= 2^128 set `bad`.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void split_f64(double v, float &hi, float &lo24, int &bad) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -38,10 +46,12 @@ __device__ __forceinline__ void split_f64(double v, float &hi, float &lo24, int 
     // 52-bit mantissa m = [h32 & 0xFFFFF : l32]; hi keeps its top 23 bits.
     const unsigned int mhi = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
     hi = __uint_as_float(sign | ((unsigned int)e32 << 23) | mhi);
-    // The remaining 29 bits (l32 & 0x1FFFFFFF) weigh 2^(e - 1023 - 52); times
-    // 2^24 that is the float exponent field e32 - 28.
-    const unsigned int rem = l32 & 0x1FFFFFFFu;
-    const float r = __uint2float_rz(rem) * __uint_as_float((unsigned int)(e32 > 28 ? e32 - 28 : 1) << 23);
+    // The top 24 of the remaining 29 bits, (l32 & 0x1FFFFFFF) >> 5, weigh
+    // 2^(e - 1023 - 47) each; times 2^24 that is the float exponent field e32 - 23.
+    const unsigned int rem = (l32 & 0x1FFFFFFFu) >> 5;
+    const float m = __uint_as_float(0x4B000000u | (rem & 0x7FFFFFu)) - 0x1p23f;   // low 23 bits, exact
+    const float q = m + ((rem >> 23) ? 0x1p23f : 0.0f);                           // < 2^24, exact
+    const float r = q * __uint_as_float((unsigned int)(e32 > 28 ? e32 - 23 : 1) << 23);
     lo24 = (e32 > 28) ? (sign ? -r : r) : 0.0f;
 }
 
@@ -98,56 +108,195 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
     return r;
 }
 
-// Gershgorin discs: one warp per row.  Each off-diagonal |H_ij| is unpacked
-// with integer operations into |hi| + 2^-24 |lo24|, which falls short of it by
-// less than 2^-47 relative (2^-121 absolute for tiny entries); the |hi| are
-// summed in compensated FP32 pairs and the |lo24| in FP32.  The radius is then
-// widened to r (1 + 2^-36) + 2^-50 |d| + N 2^-120, which covers the cut, the
-// sums and the rounding of d -/+ r, so the bounds contain every exact disc and
-// exceed it by about 2^-36 relative.  Centres and bounds are FP64.
-__global__ void __launch_bounds__(AUX_THREADS) k_gershgorin(InstDesc *inst) {
+// ---------------------------------------------------------------------------
+// Passes over the lower triangle.  H is symmetric, so the bounds, the input
+// layer and the output read only its 64 x 64 tiles (ti, tj) with tj <= ti, and
+// write what lies above the diagonal from the transposed tile.  A warp owns
+// eight rows of a tile (w, w + 8, ...) and each lane two adjacent columns, so
+// that every row of the tile is one 512-byte FP64 access per warp and a thread
+// has sixteen loads in flight before it uses any.
+// ---------------------------------------------------------------------------
+constexpr int AT = 64;                             // tile side
+constexpr int AT_RPW = AT / (AUX_THREADS / 32);    // rows per warp: 8
+constexpr int AT_BLOCKS_PER_SM = 4;                // residency the tile kernels are compiled for
+constexpr int FIN_BLOCKS_PER_SM = 3;               // the output kernel's (sixteen FP64 loads per thread)
+
+// k -> (ti, tj), tj <= ti, row-major over the lower triangle of tiles: an FP32
+// root (FP64 is slow on this GPU) corrected to the exact integer.
+__device__ __forceinline__ void lower_tile(long long k, int &ti, int &tj) {
+    int t = (int)((sqrtf(8.0f * (float)k + 1.0f) - 1.0f) * 0.5f);
+    while ((long long)(t + 1) * (t + 2) / 2 <= k) ++t;
+    while ((long long)t * (t + 1) / 2 > k) --t;
+    ti = t;
+    tj = (int)(k - (long long)t * (t + 1) / 2);
+}
+
+// (M_ij, M_i,j+1) of an n x n FP64 matrix, j even, zero outside it; one 16-byte load
+// when `vec` (n even and M 16-byte aligned).
+__device__ __forceinline__ void load_pair(const double *__restrict__ M, int n, bool vec, int i, int j, double &a,
+                                          double &b) {
+    a = 0.0;
+    b = 0.0;
+    if (i >= n || j >= n) return;
+    const double *p = M + (size_t)i * n + j;
+    if (vec) {
+        const double2 v = *(const double2 *)p;
+        a = v.x;
+        b = v.y;
+    } else {
+        a = p[0];
+        if (j + 1 < n) b = p[1];
+    }
+}
+
+// (out_ij, out_i,j+1) = (a, b) inside the n x n matrix, j even; one 8-byte store when `vec`.
+__device__ __forceinline__ void store_pair(float *__restrict__ out, int n, bool vec, int i, int j, float a, float b) {
+    if (i >= n || j >= n) return;
+    float *p = out + (size_t)i * n + j;
+    if (vec) {
+        *(float2 *)p = make_float2(a, b);
+    } else {
+        p[0] = a;
+        if (j + 1 < n) p[1] = b;
+    }
+}
+
+// Compensated sum of the 16 floats v[0], v[stride], ..., v[15 stride].
+__device__ __forceinline__ FF ff_chain16(const float *v, int stride) {
+    FF a = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) ff_add(a, v[k * stride]);
+    return a;
+}
+
+// Sum of the 64 floats v[0], v[stride], ..., v[63 stride]: four compensated chains
+// of sixteen, combined pairwise.
+__device__ __forceinline__ FF ff_sum64(const float *v, int stride) {
+    FF a = ff_chain16(v, stride), b = ff_chain16(v + 16 * stride, stride);
+    FF c = ff_chain16(v + 32 * stride, stride), e = ff_chain16(v + 48 * stride, stride);
+    ff_add_ff(a, b);
+    ff_add_ff(c, e);
+    ff_add_ff(a, c);
+    return a;
+}
+
+__device__ __forceinline__ float f_sum64(const float *v, int stride) {
+    float a = 0.0f;
+#pragma unroll 16
+    for (int k = 0; k < 64; ++k) a += v[k * stride];
+    return a;
+}
+
+// Gershgorin discs, first pass: per lower tile, the absolute off-diagonal entries
+// are unpacked with integer operations into |hi| + 2^-24 |lo24| (short of |H_ij| by
+// < 2^-47 relative, or by < 2^-121 absolute for tiny entries) and staged in shared
+// memory.  One thread per tile row sums its row (the rows of tile row ti, column
+// block tj) and one thread per tile column its column (by symmetry, the rows of
+// tile row tj, column block ti), so that row i receives exactly one partial per
+// column block b, stored in P[b n + i]; a diagonal tile gives each of its rows one
+// partial from its row and its column.  The |hi| of a partial are summed as four
+// (diagonal tile: eight) compensated FP32 chains of sixteen combined pairwise, the
+// |lo24| in FP32, and the partial is converted to FP64 once: its error is below
+// 2^-39 of its value.  P is the second FP32 master buffer (4 np^2 bytes, at least
+// 8 n ceil(n / 64) are needed), which nothing uses before the layers.
+__global__ void __launch_bounds__(AUX_THREADS, AT_BLOCKS_PER_SM) k_gersh_tiles(InstDesc *inst) {
+    __shared__ float sh[AT][AT + 1], sl[AT][AT + 1];
     const InstDesc &d = inst[blockIdx.y];
     const int n = d.n;
+    const double *__restrict__ H = d.H;
+    double *__restrict__ P = (double *)d.xf[1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double lo = INFINITY, hi = -INFINITY;
+    const int nt = (n + AT - 1) / AT;
+    const long long ntiles = (long long)nt * (nt + 1) / 2;
+    const bool vec = ((n & 1) == 0) && (((uintptr_t)H & 15) == 0);
     int bad = 0;
-    for (int row = blockIdx.x * (AUX_THREADS / 32) + w; row < n; row += gridDim.x * (AUX_THREADS / 32)) {
-        const double *__restrict__ h = d.H + (size_t)row * n;
-        FF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
-        float acc_lo = 0.0f;  // sum of the 2^24-scaled low parts
-        for (int j0 = lane; j0 < n; j0 += 32 * 8) {
-            double v[8];
+    for (long long k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        int ti, tj;
+        lower_tile(k, ti, tj);
+        const int i0 = ti * AT, j0 = tj * AT, c0 = 2 * lane;
+        const bool dg = (ti == tj);
+        double h[AT_RPW][2];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = j0 + 32 * u;
-                v[u] = (j < n) ? h[j] : 0.0;
-            }
+        for (int q = 0; q < AT_RPW; ++q) load_pair(H, n, vec, i0 + w + 8 * q, j0 + c0, h[q][0], h[q][1]);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = j0 + 32 * u;
+        for (int q = 0; q < AT_RPW; ++q) {
+            const int r = w + 8 * q;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int c = c0 + e;
                 float a, b;
-                split_f64(v[u], a, b, bad);
-                if (j != row) {
-                    ff_add(acc[u & 1], fabsf(a));
-                    acc_lo += fabsf(b);
-                }
+                split_f64(h[q][e], a, b, bad);   // zero outside the matrix
+                const bool keep = !dg || c < r;  // strictly below the diagonal
+                sh[r][c] = keep ? fabsf(a) : 0.0f;
+                sl[r][c] = keep ? fabsf(b) : 0.0f;
             }
         }
-        double rs = warp_sum_d(ff_value(acc[0]) + ff_value(acc[1]) + (double)acc_lo * 0x1p-24);
-        rs = __shfl_sync(0xffffffffu, rs, 0);
-        const double dv = h[row];
-        if (!isfinite(dv)) bad = 1;
-        rs = rs * (1.0 + 0x1p-36) + fabs(dv) * 0x1p-50 + (double)n * 0x1p-120;
-        lo = fmin(lo, dv - rs);
-        hi = fmax(hi, dv + rs);
+        __syncthreads();
+        const int t = threadIdx.x;
+        if (t < AT) {                         // rows of tile row ti
+            FF a = ff_sum64(&sh[t][0], 1);
+            float lo = f_sum64(&sl[t][0], 1);
+            if (dg) {                         // and the column part of the diagonal tile
+                ff_add_ff(a, ff_sum64(&sh[0][t], AT + 1));
+                lo += f_sum64(&sl[0][t], AT + 1);
+            }
+            if (i0 + t < n) P[(size_t)tj * n + i0 + t] = (double)a.s + (double)a.c + (double)lo * 0x1p-24;
+        } else if (t < 2 * AT && !dg) {       // rows of tile row tj, from column block ti
+            const int c = t - AT;
+            FF a = ff_sum64(&sh[0][c], AT + 1);
+            const float lo = f_sum64(&sl[0][c], AT + 1);
+            if (j0 + c < n) P[(size_t)ti * n + j0 + c] = (double)a.s + (double)a.c + (double)lo * 0x1p-24;
+        }
+        __syncthreads();
     }
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) {
-        if (lo <= hi) {
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0 && bad) atomicOr(&d.ctl->nonfinite, 1);
+}
+
+// Gershgorin discs, second pass: per row the FP64 sum of its partials (warp w of a
+// block adds column blocks w, w + 8, ... for 32 consecutive rows, then the eight
+// sums are added in warp order; error < 2^-45 of the sum for n <= 65536), then
+// the radius widened to r (1 + 2^-36) + 2^-50 |d| + N 2^-120, which covers the
+// unpacking cut, both passes' sums and the rounding of d -/+ r, so the bounds
+// contain every exact disc and exceed it by about 2^-36 relative.  Centres and
+// bounds are FP64; each block folds its extreme disc ends into the order-
+// preserving keys with one atomic each.
+constexpr int GR_ROWS = 32;   // rows per block of the second pass
+__global__ void __launch_bounds__(AUX_THREADS) k_gersh_rows(InstDesc *inst) {
+    __shared__ double sp[AUX_THREADS / 32][GR_ROWS];
+    const InstDesc &d = inst[blockIdx.y];
+    const int n = d.n;
+    const double *__restrict__ P = (const double *)d.xf[1];
+    const int nt = (n + AT - 1) / AT;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = blockIdx.x * GR_ROWS + lane;
+    if (blockIdx.x * GR_ROWS >= n) return;   // block-uniform
+    double part = 0.0;
+    if (row < n) {
+#pragma unroll 4
+        for (int b = w; b < nt; b += AUX_THREADS / 32) part += P[(size_t)b * n + row];
+    }
+    sp[w][lane] = part;
+    __syncthreads();
+    if (w == 0) {
+        double lo = INFINITY, hi = -INFINITY;
+        if (row < n) {
+            double rs = 0.0;
+#pragma unroll
+            for (int k = 0; k < AUX_THREADS / 32; ++k) rs += sp[k][lane];
+            const double dv = d.H[(size_t)row * n + row];
+            rs = rs * (1.0 + 0x1p-36) + fabs(dv) * 0x1p-50 + (double)n * 0x1p-120;
+            lo = dv - rs;
+            hi = dv + rs;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0 && lo <= hi) {
             atomicMin(&d.ctl->emin_key, dkey(lo));
             atomicMax(&d.ctl->emax_key, dkey(hi));
         }
-        if (bad) atomicOr(&d.ctl->nonfinite, 1);
     }
 }
 
@@ -272,6 +421,139 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_x(InstDesc *inst, int user
     }
 }
 
+// The 16-bit split (hi, lo) of two adjacent values, as packed pairs (element j in
+// the low half): the same values as split2 gives one at a time, from conversions
+// of two floats at once and exact scaling in the 16-bit domain.
+template <int PREC, int SHIFT>
+__device__ __forceinline__ void split2_pair(float a, float b, uint32_t &hi, uint32_t &lo) {
+    if (PREC == SP2_FP16_SPLIT) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 hs = __hmul2(h, __float2half2_rn((float)(1 << SHIFT)));   // exact (|x| <= 1)
+        const __half2 l = __floats2half2_rn(__fsub_rn(a, hf.x) * (float)(1 << SHIFT),
+                                            __fsub_rn(b, hf.y) * (float)(1 << SHIFT));
+        hi = *reinterpret_cast<const uint32_t *>(&hs);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(__fsub_rn(a, hf.x), __fsub_rn(b, hf.y));
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+// X_0 on the tensor-core path, from the lower triangle of H.  A tile (ti, tj) below
+// the diagonal gives X_0 there, its FP32 master (the layers and the output read
+// the master on and below the diagonal only) and the split operands of
+// Y_0 = X_0 - I/2, and, transposed through shared memory, the split operands of
+// the mirror tile (tj, ti); a diagonal tile is read and written whole.  Each
+// element is the same function of H_ij as in the full pass, so X_0 is the same
+// for a symmetric H; ||X_0||_F^2 counts a tile below the diagonal twice.
+template <int PREC>
+__global__ void __launch_bounds__(AUX_THREADS, AT_BLOCKS_PER_SM) k_init_x_tc(InstDesc *inst, int user_bounds) {
+    __shared__ uint32_t sp[AT][AT + 1];   // (hi | lo << 16) of the tile, for the mirror
+    const InstDesc &d = inst[blockIdx.y];
+    const int n = d.n, np = d.np;
+    double emin, emax;
+    resolve_bounds(d, user_bounds != 0, emin, emax);
+    const double delta = emax - emin;
+    const bool degenerate = !(delta > 0.0) || !isfinite(delta) || d.ctl->nonfinite;
+    const double inv = degenerate ? 0.0 : 1.0 / delta;
+    const float inv_hi = (float)inv;                 // 1/delta as a float pair
+    const float inv_lo = (float)(inv - (double)inv_hi);
+    const float inv_lo24 = inv_hi * 0x1p-24f;       // weight of the 2^24-scaled low part
+    int bad_unused = 0;
+    const double *__restrict__ H = d.H;
+    float *__restrict__ xf = xmaster(d, 0, false);
+    uint16_t *__restrict__ op1 = d.xop;                    // hi
+    uint16_t *__restrict__ op2 = d.xop + (size_t)np * np;  // lo
+    // ft: Tr X_0; fq: ||X_0||_F^2; fw: ||Y_0||_F^2 - ||X_0||_F^2, which only the
+    // diagonal (y = x - 1/2 there) contributes.
+    FF ft = {0.f, 0.f}, fq = {0.f, 0.f}, fw = {0.f, 0.f};
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, c0 = 2 * lane;
+    const int nt = np / AT;                          // np is a multiple of 128
+    const long long ntiles = (long long)nt * (nt + 1) / 2;
+    const bool vec = ((n & 1) == 0) && (((uintptr_t)H & 15) == 0);
+    for (long long k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        int ti, tj;
+        lower_tile(k, ti, tj);
+        const int i0 = ti * AT, j0 = tj * AT;
+        const bool dg = (ti == tj);
+        double h[AT_RPW][2];
+#pragma unroll
+        for (int q = 0; q < AT_RPW; ++q) load_pair(H, n, vec, i0 + w + 8 * q, j0 + c0, h[q][0], h[q][1]);
+        const float wq = dg ? 1.0f : 2.0f;
+#pragma unroll
+        for (int q = 0; q < AT_RPW; ++q) {
+            const int r = w + 8 * q, i = i0 + r;
+            float x[2], yy[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int j = j0 + c0 + e;
+                float v = 0.0f, y = 0.0f;
+                if (i < n && j < n) {
+                    if (i == j) {
+                        // the diagonal in FP64 (emax - H_ii) / delta; its terms of the diagonal sums
+                        v = (float)((emax - h[q][e]) * inv);
+                        y = v - 0.5f;
+                        ff_add(ft, v);
+                        ff_add_sq(fw, y, 1.0f);
+                        ff_add_sq(fw, v, -1.0f);
+                    } else {
+                        float a, lo24;  // -h / (eps_max - eps_min): one rounding of a sum of small terms
+                        split_f64(h[q][e], a, lo24, bad_unused);
+                        v = -fmaf(a, inv_hi, fmaf(a, inv_lo, lo24 * inv_lo24));
+                        y = v;
+                    }
+                }
+                ff_add_sq(fq, v, wq);
+                x[e] = v;
+                yy[e] = y;
+            }
+            uint32_t hp, lp;   // (hi, lo) of columns c0, c0 + 1
+            split2_pair<PREC, X_SHIFT>(yy[0], yy[1], hp, lp);
+            if (!dg) {
+                sp[r][c0] = __byte_perm(hp, lp, 0x5410);       // hi | lo << 16 of column c0
+                sp[r][c0 + 1] = __byte_perm(hp, lp, 0x7632);   // ... and of column c0 + 1
+            }
+            const size_t idx = (size_t)i * np + j0 + c0;
+            *(float2 *)(xf + idx) = make_float2(x[0], x[1]);
+            *(uint32_t *)(op1 + idx) = hp;
+            *(uint32_t *)(op2 + idx) = lp;
+        }
+        if (!dg) {  // block-uniform
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < AT_RPW; ++q) {
+                const int r = w + 8 * q;   // mirror row j0 + r, columns i0 + c0, i0 + c0 + 1
+                const uint32_t u0 = sp[c0][r], u1 = sp[c0 + 1][r];
+                const size_t idx = (size_t)(j0 + r) * np + i0 + c0;
+                *(uint32_t *)(op1 + idx) = __byte_perm(u0, u1, 0x5410);
+                *(uint32_t *)(op2 + idx) = __byte_perm(u0, u1, 0x7632);
+            }
+            __syncthreads();
+        }
+    }
+    ff_add_ff(fw, fq);   // ||Y_0||_F^2
+    double3 s = block_sum3(ff_value(ft), ff_value(fq), ff_value(fw));
+    if (threadIdx.x == 0) {
+        Part pr;
+        pr.t = s.x;
+        pr.q = s.y;
+        pr.w = s.z;
+        pr.p = 0.0;
+        d.part[0][blockIdx.x] = pr;
+        if (blockIdx.x == 0) {
+            d.ctl->init_parts = gridDim.x;
+            d.ctl->eps_min = emin;
+            d.ctl->eps_max = emax;
+            if (d.ctl->nonfinite) d.ctl->status = SP2_ERR_NONFINITE;
+            else if (degenerate) d.ctl->degenerate = 1;
+        }
+    }
+}
+
 // X_0 given directly (FP32, n x n), for the layer-application entry point.
 template <int PATH, int PREC>
 __global__ void __launch_bounds__(AUX_THREADS) k_init_x_from(InstDesc *inst, const float *X0) {
@@ -344,16 +626,18 @@ __global__ void __launch_bounds__(AUX_THREADS) k_init_y(InstDesc *inst, int mode
 }
 
 // D = X_L (un-padded copy, diagonal offset added), FP64 partials of Tr[D H] and
-// Tr D per block; the response / adjoint output is the Y stream with its scale
-// removed.  The layer kernels keep only the lower triangle and the diagonal of
-// the FP32 masters current (the next layer reads nothing else), so the output
-// is assembled from 32 x 32 lower-triangle tiles (ti >= tj) staged in shared
-// memory: each tile is written to (ti, tj) and, transposed, to (tj, ti), both
-// with coalesced rows.  H is symmetric, so Tr[D H] is summed over the lower
-// triangle with off-diagonal weight 2.
-// Eight blocks per SM (32 registers per thread at most): the 1024 blocks then run as one wave.
-__global__ void __launch_bounds__(AUX_THREADS, 8) k_finalize(InstDesc *inst, int mode) {
-    __shared__ float sx[32][33], sy[32][33];
+// Tr D per block; the response / adjoint output (SECOND) is the Y stream with its
+// scale removed.  The layer kernels keep only the lower triangle and the diagonal
+// of the FP32 masters current (the next layer reads nothing else), so the output
+// is assembled from the lower 64 x 64 tiles: a tile below the diagonal is written
+// to (ti, tj) from registers and, transposed through shared memory, to (tj, ti); a
+// diagonal tile is completed from its lower half.  H is symmetric, so Tr[D H] is
+// summed over the lower triangle with off-diagonal weight 2.  d.fin_blocks blocks
+// per instance, as many as are resident at once.
+template <bool SECOND>
+__global__ void __launch_bounds__(AUX_THREADS, SECOND ? 2 : FIN_BLOCKS_PER_SM) k_finalize(InstDesc *inst, int mode) {
+    __shared__ float sx[AT][AT + 1];
+    __shared__ float sy[SECOND ? AT : 1][AT + 1];
     const InstDesc &d = inst[blockIdx.y];
     if (blockIdx.x >= d.fin_blocks) return;
     const int n = d.n, np = d.np;
@@ -364,7 +648,6 @@ __global__ void __launch_bounds__(AUX_THREADS, 8) k_finalize(InstDesc *inst, int
     float *__restrict__ out = d.out;
     float *__restrict__ out1 = d.out1;
     const float xoff = (float)ctl->x_offset;
-    const bool second = (mode == MODE_RESPONSE || mode == MODE_ADJOINT);
     float ys = 0.0f;
     if (mode == MODE_RESPONSE) ys = (float)(1.0 / ctl->y_scale);
     if (mode == MODE_ADJOINT) ys = (float)(-1.0 / (ctl->y_scale * (ctl->eps_max - ctl->eps_min)));
@@ -372,56 +655,84 @@ __global__ void __launch_bounds__(AUX_THREADS, 8) k_finalize(InstDesc *inst, int
     // into product and error (FMA), all summed in a compensated FP32 pair.
     FF fe = {0.f, 0.f}, ftr = {0.f, 0.f};   // compensated FP32 pairs (FP64 is slow on this part)
     int bad_unused = 0;
-    const int tc = threadIdx.x & 31, tr0 = threadIdx.x >> 5;   // tile column, first tile row
-    const int nt = (n + 31) / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, c0 = 2 * lane;
+    const int nt = (n + AT - 1) / AT;
     const long long ntiles = (long long)nt * (nt + 1) / 2;
+    const bool hvec = ((n & 1) == 0) && (((uintptr_t)H & 15) == 0);
+    const bool ovec = ((n & 1) == 0) && (((uintptr_t)out & 7) == 0);
+    const bool ovec1 = ((n & 1) == 0) && (((uintptr_t)out1 & 7) == 0);
     for (long long k = blockIdx.x; k < ntiles; k += d.fin_blocks) {
-        // k -> (ti, tj) with tj <= ti, row-major over the lower triangle of tiles: an FP32
-        // root (FP64 is slow on this GPU) corrected to the exact integer below
-        int ti = (int)((sqrtf(8.0f * (float)k + 1.0f) - 1.0f) * 0.5f);
-        while ((long long)(ti + 1) * (ti + 2) / 2 <= k) ++ti;
-        while ((long long)ti * (ti + 1) / 2 > k) --ti;
-        const int tj = (int)(k - (long long)ti * (ti + 1) / 2);
-        const int i0 = ti * 32, j0 = tj * 32;
+        int ti, tj;
+        lower_tile(k, ti, tj);
+        const int i0 = ti * AT, j0 = tj * AT;
+        const bool dg = (ti == tj);
+        float2 x[AT_RPW], yv[SECOND ? AT_RPW : 1];
+        double h[AT_RPW][2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int r = tr0 + 8 * q, i = i0 + r, j = j0 + tc;
-            float x = 0.0f, yv = 0.0f;
-            if (i < n && j < n && (ti > tj || r >= tc)) {
-                x = X[(size_t)i * np + j];
-                if (i == j) {
-                    x += xoff;  // true X_L = stored X_L + c_L I
-                    ff_add(ftr, x);
+        for (int q = 0; q < AT_RPW; ++q) {
+            const int i = i0 + w + 8 * q;
+            // rows below n lie inside the padded np x np masters
+            x[q] = (i < n) ? *(const float2 *)(X + (size_t)i * np + j0 + c0) : make_float2(0.f, 0.f);
+            if (SECOND) yv[q] = (i < n) ? *(const float2 *)(Y + (size_t)i * np + j0 + c0) : make_float2(0.f, 0.f);
+            if (H) load_pair(H, n, hvec, i, j0 + c0, h[q][0], h[q][1]);
+        }
+#pragma unroll
+        for (int q = 0; q < AT_RPW; ++q) {
+            const int r = w + 8 * q, i = i0 + r;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int c = c0 + e, j = j0 + c;
+                float xv = e ? x[q].y : x[q].x;
+                float yw = 0.0f;
+                if (SECOND) yw = (e ? yv[q].y : yv[q].x) * ys;
+                if (!(i < n && j < n && (!dg || c <= r))) {
+                    xv = 0.0f;   // outside the matrix, or above the diagonal (stale)
+                    yw = 0.0f;
+                } else {
+                    if (i == j) {
+                        xv += xoff;  // true X_L = stored X_L + c_L I
+                        ff_add(ftr, xv);
+                    }
+                    if (H) {
+                        float h1, h2;
+                        split_f64(h[q][e], h1, h2, bad_unused);
+                        const float wgt = (i == j) ? 1.0f : 2.0f;
+                        const float p = __fmul_rn(xv, h1);
+                        const float perr = __fmaf_rn(xv, h1, -p);
+                        ff_add(fe, __fmul_rn(wgt, p));
+                        fe.c = __fadd_rn(fe.c, __fmul_rn(wgt, __fmaf_rn(xv, h2 * 0x1p-24f, perr)));
+                    }
                 }
-                if (H) {
-                    float h1, h2;
-                    split_f64(H[(size_t)i * n + j], h1, h2, bad_unused);
-                    const float wgt = (j == i) ? 1.0f : 2.0f;
-                    const float p = __fmul_rn(x, h1);
-                    const float perr = __fmaf_rn(x, h1, -p);
-                    ff_add(fe, __fmul_rn(wgt, p));
-                    fe.c = __fadd_rn(fe.c, __fmul_rn(wgt, __fmaf_rn(x, h2 * 0x1p-24f, perr)));
+                sx[r][c] = xv;
+                if (SECOND) sy[r][c] = yw;
+                if (e) {
+                    x[q].y = xv;
+                    if (SECOND) yv[q].y = yw;
+                } else {
+                    x[q].x = xv;
+                    if (SECOND) yv[q].x = yw;
                 }
-                if (second) yv = Y[(size_t)i * np + j] * ys;
             }
-            sx[r][tc] = x;
-            sy[r][tc] = yv;
+            if (!dg) {
+                if (out) store_pair(out, n, ovec, i, j0 + c0, x[q].x, x[q].y);
+                if (SECOND) store_pair(out1, n, ovec1, i, j0 + c0, yv[q].x, yv[q].y);
+            }
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int r = tr0 + 8 * q;
-            const bool low = (ti > tj || r >= tc);   // the diagonal tile's upper half comes transposed
-            int i = i0 + r, j = j0 + tc;
-            if (i < n && j < n) {
-                if (out) out[(size_t)i * n + j] = low ? sx[r][tc] : sx[tc][r];
-                if (second) out1[(size_t)i * n + j] = low ? sy[r][tc] : sy[tc][r];
-            }
-            i = j0 + r;
-            j = i0 + tc;
-            if (ti > tj && i < n && j < n) {        // the mirror tile (tj, ti)
-                if (out) out[(size_t)i * n + j] = sx[tc][r];
-                if (second) out1[(size_t)i * n + j] = sy[tc][r];
+        for (int q = 0; q < AT_RPW; ++q) {
+            const int r = w + 8 * q;
+            if (dg) {  // the diagonal tile's upper half is its lower half transposed
+                const int ca = c0, cb = c0 + 1;
+                const float a = r >= ca ? sx[r][ca] : sx[ca][r], b = r >= cb ? sx[r][cb] : sx[cb][r];
+                if (out) store_pair(out, n, ovec, i0 + r, i0 + c0, a, b);
+                if (SECOND) {
+                    const float a1 = r >= ca ? sy[r][ca] : sy[ca][r], b1 = r >= cb ? sy[r][cb] : sy[cb][r];
+                    store_pair(out1, n, ovec1, i0 + r, i0 + c0, a1, b1);
+                }
+            } else {   // the mirror tile (tj, ti): row j0 + r, columns i0 + c0, i0 + c0 + 1
+                if (out) store_pair(out, n, ovec, j0 + r, i0 + c0, sx[c0][r], sx[c0 + 1][r]);
+                if (SECOND) store_pair(out1, n, ovec1, j0 + r, i0 + c0, sy[c0][r], sy[c0 + 1][r]);
             }
         }
         __syncthreads();
@@ -460,10 +771,36 @@ int grid_for(size_t work, int per_block, int cap) {
 
 }  // namespace
 
+// Streaming multiprocessors of the current device (0 if the query fails).
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
+}
+
+// Lower 64 x 64 tiles of an n x n matrix.
+static long long lower_tiles(int n) {
+    const long long nt = (n + AT - 1) / AT;
+    return nt * (nt + 1) / 2;
+}
+
+// Blocks of a lower-triangle pass over up to `tiles` tiles: as many as are resident at once.
+static int tile_grid(long long tiles) {
+    const int sms = sm_count();
+    const long long cap = (long long)(sms > 0 ? sms : 1) * AT_BLOCKS_PER_SM;
+    return (int)std::max(1LL, std::min(tiles, cap));
+}
+
 cudaError_t launch_gershgorin(InstDesc *inst, int B, int max_n, bool user_bounds, cudaStream_t s) {
     (void)user_bounds;  // bounds are computed anyway: the same pass detects non-finite input
-    dim3 grid(grid_for((size_t)max_n, AUX_THREADS / 32, 2048), B);
-    k_gershgorin<<<grid, AUX_THREADS, 0, s>>>(inst);
+    k_gersh_tiles<<<dim3(tile_grid(lower_tiles(max_n)), B), AUX_THREADS, 0, s>>>(inst);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gersh_rows<<<dim3((max_n + GR_ROWS - 1) / GR_ROWS, B), AUX_THREADS, 0, s>>>(inst);
     return cudaGetLastError();
 }
 
@@ -478,13 +815,17 @@ int init_blocks_for(int np) { return np < INIT_BLOCKS_MAX ? np : INIT_BLOCKS_MAX
 
 cudaError_t launch_init_x(InstDesc *inst, int B, int max_np, int path, int precision, bool user_bounds,
                           cudaStream_t s) {
-    dim3 grid(init_blocks_for(max_np), B);
     // Every instance must be covered by the same number of blocks it reports in
-    // init_parts: the grid-stride loop handles any np with this grid.
+    // init_parts (at most init_blocks_for(max_np), the partial buffers' floor): the
+    // grid-stride loops handle any np with these grids.
     const int ub = user_bounds ? 1 : 0;
-    if (path == PATH_SIMT) k_init_x<PATH_SIMT, SP2_FP16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, ub);
-    else if (precision == SP2_BF16_SPLIT) k_init_x<PATH_TC, SP2_BF16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, ub);
-    else k_init_x<PATH_TC, SP2_FP16_SPLIT><<<grid, AUX_THREADS, 0, s>>>(inst, ub);
+    if (path == PATH_SIMT) {
+        k_init_x<PATH_SIMT, SP2_FP16_SPLIT><<<dim3(init_blocks_for(max_np), B), AUX_THREADS, 0, s>>>(inst, ub);
+        return cudaGetLastError();
+    }
+    const int g = std::min(init_blocks_for(max_np), tile_grid(lower_tiles(max_np)));
+    if (precision == SP2_BF16_SPLIT) k_init_x_tc<SP2_BF16_SPLIT><<<dim3(g, B), AUX_THREADS, 0, s>>>(inst, ub);
+    else k_init_x_tc<SP2_FP16_SPLIT><<<dim3(g, B), AUX_THREADS, 0, s>>>(inst, ub);
     return cudaGetLastError();
 }
 
@@ -505,10 +846,15 @@ cudaError_t launch_init_y(InstDesc *inst, int mode, int precision, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(InstDesc *inst, int B, int max_n, int mode, cudaStream_t s) {
-    (void)max_n;
-    dim3 grid(FIN_BLOCKS_MAX, B);
-    k_finalize<<<grid, AUX_THREADS, 0, s>>>(inst, mode);
+int finalize_blocks() {
+    const int sms = sm_count();
+    return std::min(FIN_BLOCKS_MAX, (sms > 0 ? sms : 1) * FIN_BLOCKS_PER_SM);
+}
+
+cudaError_t launch_finalize(InstDesc *inst, int B, int fin_blocks, int mode, cudaStream_t s) {
+    dim3 grid(fin_blocks, B);
+    if (mode == MODE_RESPONSE || mode == MODE_ADJOINT) k_finalize<true><<<grid, AUX_THREADS, 0, s>>>(inst, mode);
+    else k_finalize<false><<<grid, AUX_THREADS, 0, s>>>(inst, mode);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_finalize_reduce<<<B, AUX_THREADS, 0, s>>>(inst);

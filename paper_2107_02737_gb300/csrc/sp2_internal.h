@@ -143,7 +143,10 @@ cudaError_t launch_init_x(InstDesc *inst, int B, int max_np, int path, int preci
                           cudaStream_t s);
 cudaError_t launch_init_x_from(InstDesc *inst, const float *X0, int np, int path, int precision, cudaStream_t s);
 cudaError_t launch_init_y(InstDesc *inst, int mode, int precision, cudaStream_t s);
-cudaError_t launch_finalize(InstDesc *inst, int B, int max_n, int mode, cudaStream_t s);
+// Output kernel blocks per instance on the current device (the d.fin_blocks every
+// instance of a launch is given, and the grid of launch_finalize).
+int finalize_blocks();
+cudaError_t launch_finalize(InstDesc *inst, int B, int fin_blocks, int mode, cudaStream_t s);
 cudaError_t launch_fill_trivial(float *D, int n, float diag_value, cudaStream_t s);
 cudaError_t launch_simt_persistent(const RunParams &p, int grid, cudaStream_t s);
 cudaError_t launch_tc_persistent(const RunParams &p, int cta_group, int grid, cudaStream_t s);

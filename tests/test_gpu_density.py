@@ -97,6 +97,29 @@ def test_ragged_sizes(precision, cg, n):
     check_rules(res, ham.n_occ)
 
 
+@pytest.mark.parametrize("precision,cg", [("fp32", 0), ("fp16", 2), ("bf16", 1)])
+@pytest.mark.parametrize("n", [301, 1001])
+def test_odd_sizes_and_unaligned_buffers(precision, cg, n):
+    """Odd N and H, D that start off their vector alignment take the scalar paths of the
+    lower-triangle passes (bounds, input layer, output); D is the same bit for bit."""
+    ham = inputs.gapped_random(n, n // 3, inputs.rng_for(3, n))
+    D, res = sp2.density(dev(ham.H), ham.n_occ, precision=precision, cta_group=cg)
+    Dh = host(D)
+    assert res.converged
+    assert fro_err(Dh, odens.density_from_eigensystem(ham.eigvecs, ham.n_occ)) <= TOL_D[precision]
+    lo, hi = osp2.gershgorin_bounds(ham.H)
+    assert res.eps_min <= lo and res.eps_max >= hi
+    assert (res.eps_min, res.eps_max) == pytest.approx((lo, hi), rel=1e-10)
+    hbuf = torch.empty(n * n + 1, dtype=torch.float64, device="cuda")
+    hbuf[1:] = dev(ham.H).reshape(-1)
+    dbuf = torch.empty(n * n + 1, dtype=torch.float32, device="cuda")
+    D2, res2 = sp2.density(hbuf[1:].view(n, n), ham.n_occ, precision=precision, cta_group=cg,
+                           out=dbuf[1:].view(n, n))
+    assert np.array_equal(host(D2), Dh)
+    assert (res2.eps_min, res2.eps_max, res2.layers) == (res.eps_min, res.eps_max, res.layers)
+    assert res2.band_energy == res.band_energy and res2.trace_D == res.trace_D
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_banded_water_like_small(precision):
     ham = inputs.banded_tight_binding(768, inputs.rng_for(1, 768))
