@@ -24,9 +24,12 @@
  *    sp2_density_refined / sp2_density_nonorth are copied back).  Pageable host
  *    matrices, and the non-symmetric inputs G and Z, are copied whole.
  *    The caller owns every buffer it passes; the library frees none.
- *  - H must be symmetric (bit-exactly, as produced by (A + A^T)/2); the result
- *    for an asymmetric H is unspecified but finite (with pinned H it is that
- *    of the symmetric matrix with H's lower triangle).
+ *  - H must be symmetric (bit-exactly, as produced by (A + A^T)/2).  With the
+ *    split precisions the chain reads only H's lower triangle, diagonal
+ *    included (the bounds, the input layer and Tr[D H]), so its result for an
+ *    asymmetric H is that of the symmetric matrix with H's lower triangle, as
+ *    it is at any precision with pinned H; otherwise the result for an
+ *    asymmetric H is unspecified but finite.
  *  - `n_occ` must be an integer value in [0, N].  n_occ = 0 gives D = 0 and
  *    n_occ = N gives D = I without layers.
  *  - `workspace` may be NULL, in which case the call allocates device memory

@@ -447,9 +447,11 @@ __device__ __forceinline__ void split2_pair(float a, float b, uint32_t &hi, uint
 // the diagonal gives X_0 there, its FP32 master (the layers and the output read
 // the master on and below the diagonal only) and the split operands of
 // Y_0 = X_0 - I/2, and, transposed through shared memory, the split operands of
-// the mirror tile (tj, ti); a diagonal tile is read and written whole.  Each
-// element is the same function of H_ij as in the full pass, so X_0 is the same
-// for a symmetric H; ||X_0||_F^2 counts a tile below the diagonal twice.
+// the mirror tile (tj, ti); a diagonal tile completes its upper half the same way.
+// Each element is the same function of H_ij as in the full pass, so X_0 is the same
+// for a symmetric H (for any H, that of the symmetric matrix with H's lower
+// triangle, as the bounds see it); ||X_0||_F^2 counts an element below the
+// diagonal twice.
 template <int PREC>
 __global__ void __launch_bounds__(AUX_THREADS, AT_BLOCKS_PER_SM) k_init_x_tc(InstDesc *inst, int user_bounds) {
     __shared__ uint32_t sp[AT][AT + 1];   // (hi | lo << 16) of the tile, for the mirror
@@ -483,7 +485,6 @@ __global__ void __launch_bounds__(AUX_THREADS, AT_BLOCKS_PER_SM) k_init_x_tc(Ins
         double h[AT_RPW][2];
 #pragma unroll
         for (int q = 0; q < AT_RPW; ++q) load_pair(H, n, vec, i0 + w + 8 * q, j0 + c0, h[q][0], h[q][1]);
-        const float wq = dg ? 1.0f : 2.0f;
 #pragma unroll
         for (int q = 0; q < AT_RPW; ++q) {
             const int r = w + 8 * q, i = i0 + r;
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(AUX_THREADS, AT_BLOCKS_PER_SM) k_init_x_tc(Ins
             for (int e = 0; e < 2; ++e) {
                 const int j = j0 + c0 + e;
                 float v = 0.0f, y = 0.0f;
-                if (i < n && j < n) {
+                if (i < n && j < n && (!dg || c0 + e <= r)) {   // on or below the diagonal
                     if (i == j) {
                         // the diagonal in FP64 (emax - H_ii) / delta; its terms of the diagonal sums
                         v = (float)((emax - h[q][e]) * inv);
@@ -507,33 +508,40 @@ __global__ void __launch_bounds__(AUX_THREADS, AT_BLOCKS_PER_SM) k_init_x_tc(Ins
                         y = v;
                     }
                 }
-                ff_add_sq(fq, v, wq);
+                ff_add_sq(fq, v, (i == j) ? 1.0f : 2.0f);   // an element below the diagonal counts twice
                 x[e] = v;
                 yy[e] = y;
             }
             uint32_t hp, lp;   // (hi, lo) of columns c0, c0 + 1
             split2_pair<PREC, X_SHIFT>(yy[0], yy[1], hp, lp);
-            if (!dg) {
-                sp[r][c0] = __byte_perm(hp, lp, 0x5410);       // hi | lo << 16 of column c0
-                sp[r][c0 + 1] = __byte_perm(hp, lp, 0x7632);   // ... and of column c0 + 1
-            }
+            sp[r][c0] = __byte_perm(hp, lp, 0x5410);       // hi | lo << 16 of column c0
+            sp[r][c0 + 1] = __byte_perm(hp, lp, 0x7632);   // ... and of column c0 + 1
             const size_t idx = (size_t)i * np + j0 + c0;
-            *(float2 *)(xf + idx) = make_float2(x[0], x[1]);
-            *(uint32_t *)(op1 + idx) = hp;
-            *(uint32_t *)(op2 + idx) = lp;
-        }
-        if (!dg) {  // block-uniform
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < AT_RPW; ++q) {
-                const int r = w + 8 * q;   // mirror row j0 + r, columns i0 + c0, i0 + c0 + 1
-                const uint32_t u0 = sp[c0][r], u1 = sp[c0 + 1][r];
-                const size_t idx = (size_t)(j0 + r) * np + i0 + c0;
-                *(uint32_t *)(op1 + idx) = __byte_perm(u0, u1, 0x5410);
-                *(uint32_t *)(op2 + idx) = __byte_perm(u0, u1, 0x7632);
+            *(float2 *)(xf + idx) = make_float2(x[0], x[1]);   // above the diagonal of a diagonal tile: unread
+            if (!dg) {
+                *(uint32_t *)(op1 + idx) = hp;
+                *(uint32_t *)(op2 + idx) = lp;
             }
-            __syncthreads();
         }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < AT_RPW; ++q) {
+            const int r = w + 8 * q;
+            uint32_t u0, u1;
+            size_t idx;
+            if (dg) {   // block-uniform: the diagonal tile, its upper half from its lower half
+                u0 = (c0 <= r) ? sp[r][c0] : sp[c0][r];
+                u1 = (c0 + 1 <= r) ? sp[r][c0 + 1] : sp[c0 + 1][r];
+                idx = (size_t)(i0 + r) * np + i0 + c0;
+            } else {    // the mirror tile: row j0 + r, columns i0 + c0, i0 + c0 + 1
+                u0 = sp[c0][r];
+                u1 = sp[c0 + 1][r];
+                idx = (size_t)(j0 + r) * np + i0 + c0;
+            }
+            *(uint32_t *)(op1 + idx) = __byte_perm(u0, u1, 0x5410);
+            *(uint32_t *)(op2 + idx) = __byte_perm(u0, u1, 0x7632);
+        }
+        __syncthreads();
     }
     ff_add_ff(fw, fq);   // ||Y_0||_F^2
     double3 s = block_sum3(ff_value(ft), ff_value(fq), ff_value(fw));

@@ -120,6 +120,22 @@ def test_odd_sizes_and_unaligned_buffers(precision, cg, n):
     assert res2.band_energy == res.band_energy and res2.trace_D == res.trace_D
 
 
+@pytest.mark.parametrize("precision,n", [("fp16", 300), ("bf16", 1001)])
+def test_asymmetric_h_reads_the_lower_triangle(precision, n):
+    """On the tensor-core path the bounds, the input layer and the output read H's lower
+    triangle only: an H whose upper triangle is changed gives the bits of the symmetric
+    matrix built from its lower triangle."""
+    ham = inputs.gapped_random(n, n // 2, inputs.rng_for(5, n))
+    Ha = ham.H.copy()
+    iu = np.triu_indices(n, 1)
+    Ha[iu] += np.random.default_rng(6).standard_normal(iu[0].size)
+    D1, r1 = sp2.density(dev(Ha), ham.n_occ, precision=precision)
+    D2, r2 = sp2.density(dev(ham.H), ham.n_occ, precision=precision)
+    assert np.array_equal(host(D1), host(D2))
+    assert (r1.eps_min, r1.eps_max, r1.layers, r1.band_energy, r1.trace_D) == \
+        (r2.eps_min, r2.eps_max, r2.layers, r2.band_energy, r2.trace_D)
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_banded_water_like_small(precision):
     ham = inputs.banded_tight_binding(768, inputs.rng_for(1, 768))
