@@ -17,6 +17,7 @@ import dataclasses
 import os
 from typing import List, Optional, Sequence
 
+import numpy as np
 import torch
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsp2.so")
@@ -182,12 +183,18 @@ def _new_stats(cap: int = MAX_LAYERS_LIMIT + 1):
     return st
 
 
+# The layout of LayerStat as a numpy record, to read a call's layer records in one copy.
+_LAYER_DTYPE = np.dtype([("trace", "<f8"), ("trace_sq", "<f8"), ("idem", "<f8"), ("choice", "<i4"),
+                         ("reserved", "<i4"), ("alpha", "<f8")])
+assert _LAYER_DTYPE.itemsize == ctypes.sizeof(LayerStat)
+
+
 def _result(status: int, st: Stats) -> Result:
-    n = min(st.layers + 1, st.layer_cap)
-    lay = [st.layer[k] for k in range(n)]
+    n = max(0, min(st.layers + 1, st.layer_cap))
+    lay = np.frombuffer(ctypes.string_at(st.layer, n * _LAYER_DTYPE.itemsize), dtype=_LAYER_DTYPE)
     return Result(status, st.layers, st.stop_reason, st.eps_min, st.eps_max, st.band_energy, st.trace_D,
-                  [l.trace for l in lay], [l.trace_sq for l in lay], [l.idem for l in lay],
-                  [l.choice for l in lay[1:]], st, list(st.phase_ms), st.cta_group, [l.alpha for l in lay[1:]])
+                  lay["trace"].tolist(), lay["trace_sq"].tolist(), lay["idem"].tolist(), lay["choice"][1:].tolist(),
+                  st, list(st.phase_ms), st.cta_group, lay["alpha"][1:].tolist())
 
 
 def _check(status: int, where: str):

@@ -103,6 +103,23 @@ def test_layer_stat_record_layout():
     assert ctypes.sizeof(sp2.Opts) == sp2.Opts.checkpoint_stride.offset + 8
 
 
+def test_result_reads_the_layer_records():
+    st = sp2._new_stats()
+    st.layers, st.stop_reason, st.eps_min, st.cta_group = 3, 1, -2.5, 2
+    for k in range(4):
+        st.layer[k].trace, st.layer[k].trace_sq, st.layer[k].idem = 1.5 * k, 0.25 * k, 0.125 * k
+        st.layer[k].choice, st.layer[k].alpha = k % 2, 1.0 + k
+    st.layer[4].trace = 99.0   # beyond the chain: not reported
+    r = sp2._result(sp2.OK, st)
+    assert (r.layers, r.stop_reason, r.eps_min, r.cta_group) == (3, 1, -2.5, 2)
+    assert r.trace == [0.0, 1.5, 3.0, 4.5] and r.trace_sq == [0.0, 0.25, 0.5, 0.75]
+    assert r.idem == [0.0, 0.125, 0.25, 0.375]
+    assert r.choices == [1, 0, 1] and r.alphas == [2.0, 3.0, 4.0]
+    assert all(type(c) is int for c in r.choices) and all(type(t) is float for t in r.trace)
+    st.layers = 0
+    assert sp2._result(sp2.OK, st).choices == []
+
+
 def test_apply_layers_rejects_bad_choices(lib):
     X = np.zeros((4, 4), np.float32)
     ch = (ctypes.c_int * 2)(0, 2)
